@@ -1,0 +1,307 @@
+"""Benchmark of multi-level foreground estimation on GB300.
+
+One step = one fg_estimate call (all levels of Algorithm 1) on a 2048x1536 RGB image
+with FP32 storage and compute, synthetic seeded inputs already resident in HBM; L2 is
+flushed (a 256 MiB write) before every timed step, outside the timed events. The line
+also reports the 7680x4320 image, the roofline of the dominant kernel (the top-level
+pass) against the measured HBM copy bandwidth, an end-to-end figure through the C ABI
+with host buffers (copies inside the timed region), and the FP64 CPU oracle timed on
+this host's cores as a baseline.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-8k]
+Multi-GPU (torchrun, one process per GPU): every rank solves its own image (replicas,
+weak scaling); the timing is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("Mpix/s at 2048×1536 and 8K; achieved HBM GB/s vs peak; "
+          "serving p50/p99 latency")
+WORKLOAD = "single_2048x1536_hair"
+BIG = "single_7680x4320"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _traffic_from_profile(kernel_src: str, profile: str):
+    """DRAM bytes per launch recorded by ncu in profiles/, if the kernel source is unchanged
+    since the capture (the summary records the source's sha256)."""
+    path = os.path.join(ROOT, "profiles", profile)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.]+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    if not m or not h:
+        return None
+    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return float(m.group(1)) if cur == h.group(1) else None
+
+
+def cpu_baseline(sample: str, seconds: float = 10.0):
+    """The FP64 oracle, as it stands, on this host's cores: repeated full solves of the
+    workload image for about `seconds`."""
+    import oracle
+    from paper_2006_14970_gb300 import synth
+    s = synth.workload(sample)
+    h, w = s.alpha.shape
+    threads = oracle.set_threads(0)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.ml(s.I, s.alpha)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds or n >= 50:
+            break
+    return {"value": n * w * h / dt / 1e6, "unit": "Mpix/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} full FP64 solves of the {w}x{h} workload image ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    base = cpu_baseline(WORKLOAD, seconds=max(5.0, 2.0 * args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "Mpix/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 2048 * 1536 / base["value"] / 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "single_2048x1536_hair_fp32", "w": 2048, "h": 1536},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fgml", choices=["fgml", "reference"])
+    ap.add_argument("--no-8k", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2006_14970_gb300 import build as fbuild
+    fbuild.build()
+    from paper_2006_14970_gb300 import fgml, synth
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        total = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)                       # evict L2, outside the timed events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        barrier()
+        return max_over_ranks(total) / steps       # ms per step
+
+    def image_case(name):
+        s = synth.workload(name)
+        h, w = s.alpha.shape
+        I = torch.from_numpy(s.I).to(dev)
+        A = torch.from_numpy(s.alpha).to(dev)
+        F = torch.empty_like(I)
+        B = torch.empty_like(I)
+        return s, w, h, I, A, F, B
+
+    peak, peak_kind = _peaks()
+    lv_src = os.path.join(ROOT, "paper_2006_14970_gb300", "csrc", "level_pass.cu")
+
+    def top_pass_roofline(w, h, I, A, steps, warmup, profile):
+        levels = fgml.schedule(w, h)
+        (pw, ph, _), (_, _, k) = levels[-2], levels[-1]
+        Fs = torch.rand((ph, pw, 3), device=dev)
+        Bs = torch.rand((ph, pw, 3), device=dev)
+        Fd = torch.empty((h, w, 3), device=dev)
+        Bd = torch.empty((h, w, 3), device=dev)
+        ms = timed(lambda: fgml.level_pass(I, A, Fs, Bs, k, w, h, None, Fd, Bd), steps, warmup)
+        s = 4
+        algo = s * (10 * w * h + 6 * pw * ph)     # read I, alpha, previous F/B; write F, B
+        achieved = algo / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": "level_pass_kernel<float,2>", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+                "algorithmic_bytes": algo, "ms": ms,
+                "traffic": _traffic_from_profile(lv_src, profile)}
+
+    s, w, h, I, A, F, B = image_case(WORKLOAD)
+    levels = fgml.schedule(w, h)
+    n_coarse = sum(1 for (lw, lh, _) in levels if lw * lh <= 4096)
+    launches_per_step = 1 + (len(levels) - n_coarse)
+
+    with Clocks(local) as clk:
+        ms = timed(lambda: fgml.estimate(I, A, None, F, B), args.steps, args.warmup)
+        roof = top_pass_roofline(w, h, I, A, args.steps, args.warmup,
+                                 "level_pass_2048x1536.md")
+    clocks = clk.summary()
+    value = world * w * h / (ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the region
+    Ih = torch.from_numpy(s.I).pin_memory()
+    Ah = torch.from_numpy(s.alpha).pin_memory()
+    Fh = torch.empty_like(Ih).pin_memory()
+    Bh = torch.empty_like(Ih).pin_memory()
+    ms_e2e = timed(lambda: fgml.estimate_host(Ih, Ah, None, Fh, Bh), max(3, args.steps // 2),
+                   args.warmup)
+    e2e = {"value": world * w * h / (ms_e2e * 1e-3) / 1e6, "unit": "Mpix/s",
+           "h2d_bytes_per_step": int(Ih.numel() * 4 + Ah.numel() * 4),
+           "d2h_bytes_per_step": int(Fh.numel() * 4 + Bh.numel() * 4), "ms_per_step": ms_e2e}
+
+    big = None
+    if not args.no_8k:
+        del I, A, F, B
+        s8, w8, h8, I8, A8, F8, B8 = image_case(BIG)
+        ms8 = timed(lambda: fgml.estimate(I8, A8, None, F8, B8), max(3, args.steps // 2),
+                    args.warmup)
+        roof8 = top_pass_roofline(w8, h8, I8, A8, max(3, args.steps // 2), args.warmup,
+                                  "level_pass_7680x4320.md")
+        big = {"workload": "single_7680x4320_fp32", "value": world * w8 * h8 / (ms8 * 1e-3) / 1e6,
+               "unit": "Mpix/s", "ms_per_step": ms8, "roofline": roof8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(WORKLOAD)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "single_2048x1536_hair_fp32", "w": w, "h": h,
+                           "levels": len(levels), "l2": "flushed before every timed step",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+                "clocks": clocks, "cpu_baseline": cpu, "big": big,
+                "library": fgml.version()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,143 @@
+/*
+ * fgml — multi-level foreground estimation on GB300 (sm_103a).
+ *
+ * C ABI of the library libfgml.so. The method is the multi-level foreground/background
+ * estimation of Germer, Uelwer, Conrad and Harmeling, "Fast Multi-Level Foreground
+ * Estimation": given an RGB image I and an alpha matte alpha it computes a foreground F
+ * and a background B by running, on an image pyramid from 1x1 up to the input size,
+ * a fixed number of per-pixel closed-form 2x2 solves per level (Algorithm 1; the solve
+ * is the g = (U U^T + R^T V R)^{-1} (I U + R^T V h) of Section III-C).
+ *
+ * Conventions shared by every entry point
+ *  - Images are row-major, y outer, x inner. I, F and B hold 3 interleaved channels per
+ *    pixel, alpha one. row_pitch_bytes is the distance between rows in bytes; it must be
+ *    at least w * channels * element size and a multiple of the element size.
+ *  - Values are in [0, 1]. Elements are float32, bfloat16 or float16 (fg_dtype); the
+ *    solves always run in float32. All images of one call share one dtype.
+ *  - Pointers named "device" are CUDA device memory of the current device; the caller
+ *    owns them. The library owns its workspace (intermediate pyramid levels), one per
+ *    (device, stream), allocated on first use and kept until fg_release_workspace().
+ *  - Calls that take a stream are asynchronous on that stream (NULL = legacy default
+ *    stream) unless stated otherwise; errors of the launch itself are returned, errors
+ *    of the running kernels surface at the next synchronisation.
+ *  - Every entry point returns an fg_status; nothing is thrown across the ABI. The
+ *    message of the last error of the calling thread is fg_last_error().
+ *  - Widths and heights are in [1, 32767].
+ */
+#ifndef FGML_H
+#define FGML_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FG_OK = 0,
+    FG_ERR_INVALID_ARG = 1,   /* null pointer, bad size, pitch, dtype or parameter */
+    FG_ERR_OOM = 2,           /* workspace allocation failed */
+    FG_ERR_CUDA = 3,          /* a CUDA runtime call failed; see fg_last_error() */
+    FG_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    FG_ERR_RANGE = 5,         /* input outside [0, 1] or NaN (only when checked) */
+    FG_ERR_BUSY = 6,          /* a resource is in use (server full, etc.) */
+    FG_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+} fg_status;
+
+typedef enum { FG_F32 = 0, FG_BF16 = 1, FG_F16 = 2 } fg_dtype;
+
+/* Update orders. Jacobi: every pixel of sweep t+1 reads sweep t (the GPU order). */
+typedef enum { FG_ORDER_JACOBI = 0 } fg_order;
+
+/*
+ * Parameters of Algorithm 1. fg_params_default() fills the paper's values:
+ * eps_r = 5e-3 and omega = 0.1 (Section IV-F), 10 iterations on levels that fit in
+ * 32 x 32 and 2 on the others (Section III-D), clamping to [0, 1] (Algorithm 1), and a
+ * 1x1 starting F = B = 0 (Algorithm 1).
+ */
+typedef struct {
+    float eps_r;       /* regularisation epsilon_r > 0 */
+    float omega;       /* alpha-gradient weight omega >= 0 */
+    int small_size;    /* a level is "small" if w_l <= small_size and h_l <= small_size */
+    int small_iters;   /* sweeps on small levels, >= 0 */
+    int big_iters;     /* sweeps on the other levels, >= 0 */
+    int order;         /* fg_order; only FG_ORDER_JACOBI */
+    int clamp;         /* nonzero: clamp F and B to [0, 1] after each solve */
+    float init;        /* value of the 1x1 starting F and B */
+} fg_params;
+
+/* An image in memory (see the conventions above for layout and pitch). */
+typedef struct {
+    void *ptr;
+    int w;
+    int h;
+    long long row_pitch_bytes;
+    fg_dtype dtype;
+} fg_image;
+
+/* Fills *p with the paper's parameters. */
+void fg_params_default(fg_params *p);
+
+/*
+ * Level schedule of Algorithm 1 for a w x h input: n_l = max(1, ceil(log2(max(w, h))))
+ * levels; level l (1-based) is round(w^(l/n_l)) x round(h^(l/n_l)) with round(x) =
+ * floor(x + 0.5); its sweep count is small_iters if it fits in small_size x small_size,
+ * else big_iters. Writes level l to ws[l-1], hs[l-1], ks[l-1] (any of them may be
+ * NULL). Returns n_l, or -1 if w or h is out of range or n_l > cap. Host-only.
+ */
+int fg_schedule(int w, int h, const fg_params *p, int *ws, int *hs, int *ks, int cap);
+
+/*
+ * Multi-level foreground estimation (Algorithm 1) of one image, on the GPU.
+ *  I:     device, w x h x 3; alpha: device, w x h (same w, h, dtype as I).
+ *  F, B:  device, w x h x 3 outputs, same dtype; must not overlap the inputs.
+ *  params: NULL for the paper's defaults.
+ *  stream: cudaStream_t (NULL = default stream). Asynchronous.
+ * Update order: Jacobi. Levels whose F/B fit in one SM's shared memory run in one
+ * persistent block; each larger level runs as one pass (two sweeps fused) through HBM.
+ * Errors: FG_ERR_INVALID_ARG for bad images/params, FG_ERR_OOM if the workspace cannot
+ * be allocated, FG_ERR_CUDA for a failed launch.
+ */
+fg_status fg_estimate(const fg_image *I, const fg_image *alpha, const fg_params *params,
+                      fg_image *F, fg_image *B, void *stream);
+
+/*
+ * As fg_estimate, but I, alpha, F and B are HOST memory (tightly packed, element type
+ * dtype). The library copies the inputs to its device staging buffers, runs the
+ * method and copies F and B back, all on `stream`, and returns when F and B are in host
+ * memory. Page-locked host buffers give the fastest copies.
+ */
+fg_status fg_estimate_host(const void *I, const void *alpha, int w, int h, fg_dtype dtype,
+                           const fg_params *params, void *F, void *B, void *stream);
+
+/*
+ * One pass of the level update, for testing a level in isolation:
+ * the level is w x h; I_l and alpha_l are the nearest resize of the full-resolution I
+ * and alpha (Algorithm 1: resize from the input); the starting F and B are the nearest
+ * resize of (F_src, B_src) (a previous level, or this level itself); `iters` Jacobi
+ * sweeps (1..2 per pass, >2 runs several passes through the workspace) are written to
+ * (F_dst, B_dst), which must be w x h and must not overlap F_src/B_src.
+ */
+fg_status fg_level_pass(const fg_image *I, const fg_image *alpha,
+                        const fg_image *F_src, const fg_image *B_src,
+                        int iters, const fg_params *params,
+                        fg_image *F_dst, fg_image *B_dst, void *stream);
+
+/* Waits for `stream` and reports any device-side error of the library's kernels. */
+fg_status fg_sync(void *stream);
+
+/* Frees the workspace held for (current device, stream); the stream must be idle. */
+fg_status fg_release_workspace(void *stream);
+
+/* Message of the calling thread's last error ("" if none). Valid until its next call. */
+const char *fg_last_error(void);
+
+/* Version string of the library build. */
+const char *fg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGML_H */

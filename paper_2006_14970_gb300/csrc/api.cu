@@ -1,0 +1,517 @@
+// Host side of libfgml: argument checks, the level planner, per-stream workspaces and
+// the launch sequence of the multi-level method (Algorithm 1).
+#include "fgml.h"
+#include "fgml_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace fgml {
+int level_pass_strip_width();
+int level_pass_warps_per_block();
+}
+
+namespace {
+
+using namespace fgml;
+
+thread_local std::string g_err;
+
+fg_status fail(fg_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+fg_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(FG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr int kMaxSide = 32767;
+constexpr int kMaxLevels = 32;
+
+int elem_size(fg_dtype d) { return d == FG_F32 ? 4 : 2; }
+
+// ------------------------------------------------------------------ level planner
+
+// n_l = ceil(log2(max(w, h))), at least 1 (Algorithm 1).
+int level_count(int w, int h) {
+    const unsigned m = (unsigned)std::max(w, h);
+    const int n = m <= 1 ? 0 : 32 - __builtin_clz(m - 1u);
+    return std::max(n, 1);
+}
+
+// round(side^(l/n)), rounding halves up (exact halves cannot occur).
+int level_side(int side, int l, int n) {
+    return (int)std::lround(std::pow((double)side, (double)l / (double)n));
+}
+
+struct Level {
+    int w, h, k;
+};
+
+std::vector<Level> plan_levels(int w, int h, const fg_params &p) {
+    const int n = level_count(w, h);
+    std::vector<Level> lv(n);
+    for (int l = 1; l <= n; ++l) {
+        Level &L = lv[l - 1];
+        L.w = level_side(w, l, n);
+        L.h = level_side(h, l, n);
+        L.k = (L.w <= p.small_size && L.h <= p.small_size) ? p.small_iters : p.big_iters;
+    }
+    return lv;
+}
+
+// ------------------------------------------------------------------ checks
+
+fg_status check_params(const fg_params &p) {
+    if (!(p.eps_r > 0.f) || !std::isfinite(p.eps_r))
+        return fail(FG_ERR_INVALID_ARG, "eps_r must be finite and > 0");
+    if (!(p.omega >= 0.f) || !std::isfinite(p.omega))
+        return fail(FG_ERR_INVALID_ARG, "omega must be finite and >= 0");
+    if (p.small_iters < 0 || p.big_iters < 0 || p.small_size < 0)
+        return fail(FG_ERR_INVALID_ARG, "iteration counts and small_size must be >= 0");
+    if (p.small_iters > 1000000 || p.big_iters > 1000000)
+        return fail(FG_ERR_INVALID_ARG, "iteration counts above 1e6");
+    if (p.order != FG_ORDER_JACOBI)
+        return fail(FG_ERR_UNSUPPORTED, "only the Jacobi order runs on the GPU");
+    if (!std::isfinite(p.init)) return fail(FG_ERR_INVALID_ARG, "init must be finite");
+    return FG_OK;
+}
+
+fg_status check_image(const fg_image *im, int ch, const char *name) {
+    if (!im) return fail(FG_ERR_INVALID_ARG, "%s is NULL", name);
+    if (!im->ptr) return fail(FG_ERR_INVALID_ARG, "%s->ptr is NULL", name);
+    if (im->w < 1 || im->h < 1 || im->w > kMaxSide || im->h > kMaxSide)
+        return fail(FG_ERR_INVALID_ARG, "%s size %dx%d outside [1, %d]", name, im->w, im->h,
+                    kMaxSide);
+    if (im->dtype != FG_F32 && im->dtype != FG_BF16 && im->dtype != FG_F16)
+        return fail(FG_ERR_INVALID_ARG, "%s has an unknown dtype %d", name, (int)im->dtype);
+    const int es = elem_size(im->dtype);
+    if (im->row_pitch_bytes < (long long)im->w * ch * es || im->row_pitch_bytes % es)
+        return fail(FG_ERR_INVALID_ARG, "%s row pitch %lld invalid for width %d", name,
+                    im->row_pitch_bytes, im->w);
+    if (((uintptr_t)im->ptr) % es) return fail(FG_ERR_INVALID_ARG, "%s is misaligned", name);
+    return FG_OK;
+}
+
+// byte range [lo, hi) an image spans
+std::pair<uintptr_t, uintptr_t> span(const fg_image *im, int ch) {
+    const uintptr_t lo = (uintptr_t)im->ptr;
+    const uintptr_t hi = lo + (uintptr_t)(im->row_pitch_bytes * (im->h - 1)) +
+                         (uintptr_t)im->w * ch * elem_size(im->dtype);
+    return {lo, hi};
+}
+
+bool overlap(const fg_image *a, int ca, const fg_image *b, int cb) {
+    auto x = span(a, ca), y = span(b, cb);
+    return x.first < y.second && y.first < x.second;
+}
+
+// ------------------------------------------------------------------ workspaces
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Workspace {
+    Buf lev[2];   // intermediate level states: F then B, each w x h x 3
+    Buf stage;    // device staging of the host-memory entry point
+};
+
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+Workspace &workspace_for(cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    return g_ws[{current_device(), s}];
+}
+
+fg_status ensure(Buf &b, size_t need, cudaStream_t s) {
+    if (b.bytes >= need) return FG_OK;
+    if (b.p) {
+        cudaStreamSynchronize(s);   // the old buffer may still be read by queued work
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(FG_ERR_OOM, "workspace allocation of %zu bytes failed: %s", need,
+                    cudaGetErrorString(e));
+    }
+    b.bytes = need;
+    return FG_OK;
+}
+
+int sm_count() {
+    static int cache[64] = {0};
+    const int d = current_device();
+    if (d < 0 || d >= 64) return 148;
+    if (!cache[d]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
+        cache[d] = v > 0 ? v : 148;
+    }
+    return cache[d];
+}
+
+// A level state (F and B) stored inside a workspace buffer.
+struct State {
+    const void *F, *B;
+    long long pitch;   // elements
+    int w, h;
+};
+
+size_t state_bytes(int w, int h, int es) {
+    const size_t plane = ((size_t)w * h * 3 * es + 255) & ~(size_t)255;
+    return 2 * plane;
+}
+
+State state_in(const Buf &b, int w, int h, int es) {
+    const size_t plane = ((size_t)w * h * 3 * es + 255) & ~(size_t)255;
+    State s;
+    s.F = b.p;
+    s.B = (const char *)b.p + plane;
+    s.pitch = 3LL * w;
+    s.w = w;
+    s.h = h;
+    return s;
+}
+
+// ------------------------------------------------------------------ launches
+
+struct Input {
+    const void *I, *A;
+    long long I_pitch, A_pitch;   // elements
+    int w, h;
+};
+
+// Rows per warp of a level pass: enough warps for several waves of resident warps.
+int strip_rows(int w, int h) {
+    const int nx = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
+    const long long target = (long long)sm_count() * 48;   // ~4 waves of 12 warps per SM
+    long long r = ((long long)h * nx + target - 1) / target;
+    r = std::max<long long>(r, 4);
+    r = std::min<long long>(r, 512);
+    return (int)r;
+}
+
+cudaError_t pass(int dtype, int iters, int clamp, const fg_params &p, const Input &in,
+                 const State &src, void *Fd, void *Bd, long long d_pitch, int w, int h,
+                 cudaStream_t s) {
+    PassArgs a;
+    a.I = in.I;
+    a.I_pitch = in.I_pitch;
+    a.A = in.A;
+    a.A_pitch = in.A_pitch;
+    a.Iw = in.w;
+    a.Ih = in.h;
+    a.Fs = src.F;
+    a.Bs = src.B;
+    a.s_pitch = src.pitch;
+    a.sw = src.w;
+    a.sh = src.h;
+    a.Fd = Fd;
+    a.Bd = Bd;
+    a.d_pitch = d_pitch;
+    a.w = w;
+    a.h = h;
+    a.eps = p.eps_r;
+    a.omega = p.omega;
+    a.strip_h = strip_rows(w, h);
+    a.n_xstrips = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
+    a.n_warps = a.n_xstrips * ((h + a.strip_h - 1) / a.strip_h);
+    return launch_level_pass(dtype, iters, clamp, a, s);
+}
+
+// Sweep counts of the passes of a level with k sweeps: at most 2 per pass.
+std::vector<int> split_sweeps(int k) {
+    std::vector<int> v;
+    if (k == 0) {
+        v.push_back(0);
+        return v;
+    }
+    if (k % 2) v.push_back(1);
+    for (int i = 0; i < k / 2; ++i) v.push_back(2);
+    return v;
+}
+
+// Runs the passes of one level from `src` (in workspace buffer *buf, or -1 for caller
+// memory). Every pass reads one buffer and writes the other; the last pass writes to
+// (Fd, Bd) when `to_caller`, else to a workspace buffer. On return src/buf describe the
+// level's final state when it stays in the workspace.
+fg_status run_level(int dtype, const fg_params &p, const Input &in, State &src, int &buf,
+                    int k, int w, int h, bool to_caller, void *Fd, void *Bd, long long d_pitch,
+                    Workspace &ws, int es, cudaStream_t s) {
+    const std::vector<int> passes = split_sweeps(k);
+    for (size_t j = 0; j < passes.size(); ++j) {
+        if (to_caller && j + 1 == passes.size()) {
+            cudaError_t e = pass(dtype, passes[j], p.clamp, p, in, src, Fd, Bd, d_pitch, w, h, s);
+            if (e != cudaSuccess) return cuda_fail(e, "level pass launch");
+        } else {
+            const int nb = buf == 0 ? 1 : 0;
+            State dst = state_in(ws.lev[nb], w, h, es);
+            cudaError_t e = pass(dtype, passes[j], p.clamp, p, in, src, (void *)dst.F,
+                                 (void *)dst.B, dst.pitch, w, h, s);
+            if (e != cudaSuccess) return cuda_fail(e, "level pass launch");
+            src = dst;
+            buf = nb;
+        }
+    }
+    return FG_OK;
+}
+
+fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, void *Bd,
+                   long long d_pitch, cudaStream_t s) {
+    const int es = dtype == kF32 ? 4 : 2;
+    const std::vector<Level> lv = plan_levels(in.w, in.h, p);
+    const int n = (int)lv.size();
+    int nc = 0;   // levels run by the coarse kernel
+    while (nc < n && nc < kCoarseMaxLevels && (long long)lv[nc].w * lv[nc].h <= kCoarseCap) ++nc;
+
+    // workspace: every intermediate state, including extra passes of the top level
+    size_t need = 0;
+    if (nc < n) need = state_bytes(lv[nc - 1].w, lv[nc - 1].h, es);
+    for (int l = nc; l < n; ++l) {
+        const bool top = l == n - 1;
+        if (!top || split_sweeps(lv[l].k).size() > 1)
+            need = std::max(need, state_bytes(lv[l].w, lv[l].h, es));
+    }
+    Workspace &ws = workspace_for(s);
+    if (need) {
+        fg_status st = ensure(ws.lev[0], need, s);
+        if (st != FG_OK) return st;
+        st = ensure(ws.lev[1], need, s);
+        if (st != FG_OK) return st;
+    }
+
+    CoarseArgs ca;
+    std::memset(&ca, 0, sizeof ca);
+    ca.I = in.I;
+    ca.I_pitch = in.I_pitch;
+    ca.A = in.A;
+    ca.A_pitch = in.A_pitch;
+    ca.Iw = in.w;
+    ca.Ih = in.h;
+    ca.nlev = nc;
+    for (int l = 0; l < nc; ++l) {
+        ca.lw[l] = lv[l].w;
+        ca.lh[l] = lv[l].h;
+        ca.lk[l] = lv[l].k;
+    }
+    ca.eps = p.eps_r;
+    ca.omega = p.omega;
+    ca.init = p.init;
+    State src{};
+    int buf = -1;
+    if (nc == n) {
+        ca.Fd = Fd;
+        ca.Bd = Bd;
+        ca.d_pitch = d_pitch;
+    } else {
+        src = state_in(ws.lev[0], lv[nc - 1].w, lv[nc - 1].h, es);
+        buf = 0;
+        ca.Fd = (void *)src.F;
+        ca.Bd = (void *)src.B;
+        ca.d_pitch = src.pitch;
+    }
+    cudaError_t e = launch_coarse(dtype, p.clamp, ca, s);
+    if (e != cudaSuccess) return cuda_fail(e, "coarse kernel launch");
+
+    for (int l = nc; l < n; ++l) {
+        fg_status st = run_level(dtype, p, in, src, buf, lv[l].k, lv[l].w, lv[l].h, l == n - 1,
+                                 Fd, Bd, d_pitch, ws, es, s);
+        if (st != FG_OK) return st;
+    }
+    return FG_OK;
+}
+
+fg_params params_or_default(const fg_params *p) {
+    fg_params d;
+    fg_params_default(&d);
+    return p ? *p : d;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+void fg_params_default(fg_params *p) {
+    if (!p) return;
+    p->eps_r = 5e-3f;
+    p->omega = 0.1f;
+    p->small_size = 32;
+    p->small_iters = 10;
+    p->big_iters = 2;
+    p->order = FG_ORDER_JACOBI;
+    p->clamp = 1;
+    p->init = 0.f;
+}
+
+int fg_schedule(int w, int h, const fg_params *params, int *ws, int *hs, int *ks, int cap) {
+    if (w < 1 || h < 1 || w > kMaxSide || h > kMaxSide) return -1;
+    const fg_params p = params_or_default(params);
+    const std::vector<Level> lv = plan_levels(w, h, p);
+    if ((int)lv.size() > cap) return -1;
+    for (size_t i = 0; i < lv.size(); ++i) {
+        if (ws) ws[i] = lv[i].w;
+        if (hs) hs[i] = lv[i].h;
+        if (ks) ks[i] = lv[i].k;
+    }
+    return (int)lv.size();
+}
+
+fg_status fg_estimate(const fg_image *I, const fg_image *alpha, const fg_params *params,
+                      fg_image *F, fg_image *B, void *stream) {
+    g_err.clear();
+    fg_status st;
+    if ((st = check_image(I, 3, "I")) != FG_OK) return st;
+    if ((st = check_image(alpha, 1, "alpha")) != FG_OK) return st;
+    if ((st = check_image(F, 3, "F")) != FG_OK) return st;
+    if ((st = check_image(B, 3, "B")) != FG_OK) return st;
+    const fg_params p = params_or_default(params);
+    if ((st = check_params(p)) != FG_OK) return st;
+    if (alpha->w != I->w || alpha->h != I->h || F->w != I->w || F->h != I->h ||
+        B->w != I->w || B->h != I->h)
+        return fail(FG_ERR_INVALID_ARG, "I, alpha, F and B must have the same size");
+    if (alpha->dtype != I->dtype || F->dtype != I->dtype || B->dtype != I->dtype)
+        return fail(FG_ERR_INVALID_ARG, "I, alpha, F and B must have the same dtype");
+    if (F->row_pitch_bytes != B->row_pitch_bytes)
+        return fail(FG_ERR_INVALID_ARG, "F and B must have the same row pitch");
+    if (overlap(F, 3, B, 3) || overlap(F, 3, I, 3) || overlap(F, 3, alpha, 1) ||
+        overlap(B, 3, I, 3) || overlap(B, 3, alpha, 1))
+        return fail(FG_ERR_INVALID_ARG, "outputs overlap each other or the inputs");
+    const int es = elem_size(I->dtype);
+    Input in{I->ptr, alpha->ptr, I->row_pitch_bytes / es, alpha->row_pitch_bytes / es, I->w, I->h};
+    return estimate(in, (int)I->dtype, p, F->ptr, B->ptr, F->row_pitch_bytes / es,
+                    (cudaStream_t)stream);
+}
+
+fg_status fg_estimate_host(const void *I, const void *alpha, int w, int h, fg_dtype dtype,
+                           const fg_params *params, void *F, void *B, void *stream) {
+    g_err.clear();
+    if (!I || !alpha || !F || !B) return fail(FG_ERR_INVALID_ARG, "NULL host pointer");
+    if (w < 1 || h < 1 || w > kMaxSide || h > kMaxSide)
+        return fail(FG_ERR_INVALID_ARG, "size %dx%d outside [1, %d]", w, h, kMaxSide);
+    if (dtype != FG_F32 && dtype != FG_BF16 && dtype != FG_F16)
+        return fail(FG_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    const fg_params p = params_or_default(params);
+    fg_status st = check_params(p);
+    if (st != FG_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int es = elem_size(dtype);
+    const size_t n = (size_t)w * h;
+    const size_t bI = (3 * n * es + 255) & ~(size_t)255, bA = (n * es + 255) & ~(size_t)255;
+    Workspace &ws = workspace_for(s);
+    if ((st = ensure(ws.stage, 3 * bI + bA, s)) != FG_OK) return st;
+    char *dI = (char *)ws.stage.p, *dA = dI + bI, *dF = dA + bA, *dB = dF + bI;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(dI, I, 3 * n * es, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "copy of I to the device");
+    if ((e = cudaMemcpyAsync(dA, alpha, n * es, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "copy of alpha to the device");
+    Input in{dI, dA, 3LL * w, (long long)w, w, h};
+    if ((st = estimate(in, (int)dtype, p, dF, dB, 3LL * w, s)) != FG_OK) return st;
+    if ((e = cudaMemcpyAsync(F, dF, 3 * n * es, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "copy of F to the host");
+    if ((e = cudaMemcpyAsync(B, dB, 3 * n * es, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "copy of B to the host");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return FG_OK;
+}
+
+fg_status fg_level_pass(const fg_image *I, const fg_image *alpha, const fg_image *F_src,
+                        const fg_image *B_src, int iters, const fg_params *params,
+                        fg_image *F_dst, fg_image *B_dst, void *stream) {
+    g_err.clear();
+    fg_status st;
+    if ((st = check_image(I, 3, "I")) != FG_OK) return st;
+    if ((st = check_image(alpha, 1, "alpha")) != FG_OK) return st;
+    if ((st = check_image(F_src, 3, "F_src")) != FG_OK) return st;
+    if ((st = check_image(B_src, 3, "B_src")) != FG_OK) return st;
+    if ((st = check_image(F_dst, 3, "F_dst")) != FG_OK) return st;
+    if ((st = check_image(B_dst, 3, "B_dst")) != FG_OK) return st;
+    const fg_params p = params_or_default(params);
+    if ((st = check_params(p)) != FG_OK) return st;
+    if (iters < 0) return fail(FG_ERR_INVALID_ARG, "iters must be >= 0");
+    if (alpha->w != I->w || alpha->h != I->h)
+        return fail(FG_ERR_INVALID_ARG, "I and alpha must have the same size");
+    if (F_src->w != B_src->w || F_src->h != B_src->h || F_src->row_pitch_bytes != B_src->row_pitch_bytes)
+        return fail(FG_ERR_INVALID_ARG, "F_src and B_src must have the same size and pitch");
+    if (F_dst->w != B_dst->w || F_dst->h != B_dst->h || F_dst->row_pitch_bytes != B_dst->row_pitch_bytes)
+        return fail(FG_ERR_INVALID_ARG, "F_dst and B_dst must have the same size and pitch");
+    const fg_dtype dt = I->dtype;
+    if (alpha->dtype != dt || F_src->dtype != dt || B_src->dtype != dt || F_dst->dtype != dt ||
+        B_dst->dtype != dt)
+        return fail(FG_ERR_INVALID_ARG, "all images must have the same dtype");
+    if (overlap(F_dst, 3, B_dst, 3) || overlap(F_dst, 3, F_src, 3) || overlap(F_dst, 3, B_src, 3) ||
+        overlap(B_dst, 3, F_src, 3) || overlap(B_dst, 3, B_src, 3) || overlap(F_dst, 3, I, 3) ||
+        overlap(B_dst, 3, I, 3) || overlap(F_dst, 3, alpha, 1) || overlap(B_dst, 3, alpha, 1))
+        return fail(FG_ERR_INVALID_ARG, "outputs overlap each other or the inputs");
+    const int es = elem_size(dt);
+    cudaStream_t s = (cudaStream_t)stream;
+    Input in{I->ptr, alpha->ptr, I->row_pitch_bytes / es, alpha->row_pitch_bytes / es, I->w, I->h};
+    State src{F_src->ptr, B_src->ptr, F_src->row_pitch_bytes / es, F_src->w, F_src->h};
+    const int w = F_dst->w, h = F_dst->h;
+    Workspace &ws = workspace_for(s);
+    if (split_sweeps(iters).size() > 1) {
+        if ((st = ensure(ws.lev[0], state_bytes(w, h, es), s)) != FG_OK) return st;
+        if ((st = ensure(ws.lev[1], state_bytes(w, h, es), s)) != FG_OK) return st;
+    }
+    int buf = -1;   // the source is caller memory
+    return run_level((int)dt, p, in, src, buf, iters, w, h, true, F_dst->ptr, B_dst->ptr,
+                     F_dst->row_pitch_bytes / es, ws, es, s);
+}
+
+fg_status fg_sync(void *stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return FG_OK;
+}
+
+fg_status fg_release_workspace(void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace w;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        auto it = g_ws.find({current_device(), s});
+        if (it == g_ws.end()) return FG_OK;
+        w = it->second;
+        g_ws.erase(it);
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(w.lev[0].p);
+    cudaFree(w.lev[1].p);
+    cudaFree(w.stage.p);
+    return FG_OK;
+}
+
+const char *fg_last_error(void) { return g_err.c_str(); }
+
+const char *fg_version(void) { return "fgml 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// Internal declarations shared by the CUDA translation units of libfgml.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+
+namespace fgml {
+
+// ------------------------------------------------------------------ storage types
+// Images are stored as float32, bfloat16 or float16; all arithmetic is float32.
+template <typename T> __device__ __forceinline__ float ld_elem(const T *p);
+template <> __device__ __forceinline__ float ld_elem<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ld_elem<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ float ld_elem<__half>(const __half *p) {
+    return __half2float(__ldg(p));
+}
+
+template <typename T> __device__ __forceinline__ void st_elem(T *p, float v);
+template <> __device__ __forceinline__ void st_elem<float>(float *p, float v) { *p = v; }
+template <> __device__ __forceinline__ void st_elem<__nv_bfloat16>(__nv_bfloat16 *p, float v) {
+    *p = __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ void st_elem<__half>(__half *p, float v) {
+    *p = __float2half_rn(v);
+}
+
+// Centre-aligned nearest-neighbour source index of destination index d when a side of
+// length S is resized to length D: floor((2d + 1) S / (2 D)). Sides are <= 32767, so the
+// product fits in 32 bits.
+__host__ __device__ __forceinline__ int nearest_src(int d, int S, int D) {
+    return (int)(((2u * (unsigned)d + 1u) * (unsigned)S) / (2u * (unsigned)D));
+}
+
+// ------------------------------------------------------------------ kernel arguments
+struct PassArgs {
+    const void *I;          // full-resolution image, 3 channels per pixel
+    long long I_pitch;      // elements per row
+    const void *A;          // full-resolution alpha
+    long long A_pitch;      // elements per row
+    int Iw, Ih;             // full-resolution size
+    const void *Fs, *Bs;    // starting F and B (previous level or previous pass)
+    long long s_pitch;      // elements per row of Fs and Bs
+    int sw, sh;             // size of Fs and Bs
+    void *Fd, *Bd;          // output F and B of this level
+    long long d_pitch;      // elements per row of Fd and Bd
+    int w, h;               // level size
+    float eps, omega;
+    int strip_h;            // output rows per warp
+    int n_xstrips;          // strips of 60 output columns
+    int n_warps;            // n_xstrips * ceil(h / strip_h)
+};
+
+constexpr int kCoarseCap = 4096;   // pixels of the largest level the one-block kernel holds
+constexpr int kCoarseMaxLevels = 16;
+
+struct CoarseArgs {
+    const void *I;
+    long long I_pitch;
+    const void *A;
+    long long A_pitch;
+    int Iw, Ih;
+    int nlev;                              // levels 1..nlev run in the block
+    int lw[kCoarseMaxLevels], lh[kCoarseMaxLevels], lk[kCoarseMaxLevels];
+    void *Fd, *Bd;                         // F and B of level nlev
+    long long d_pitch;
+    float eps, omega, init;
+};
+
+enum DType { kF32 = 0, kBF16 = 1, kF16 = 2 };
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_level_pass(int dtype, int iters, int clamp, const PassArgs &a,
+                              cudaStream_t s);
+cudaError_t launch_coarse(int dtype, int clamp, const CoarseArgs &a, cudaStream_t s);
+size_t coarse_smem_bytes();
+
+}  // namespace fgml

@@ -1,0 +1,204 @@
+"""Python binding of libfgml (include/fgml.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module passes device
+pointers, sizes, pitches and the current torch stream through ctypes. If the shared
+library is missing it raises: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+from . import build as _build
+
+FG_OK, FG_ERR_INVALID_ARG, FG_ERR_OOM, FG_ERR_CUDA, FG_ERR_TIMEOUT, FG_ERR_RANGE, \
+    FG_ERR_BUSY, FG_ERR_UNSUPPORTED = range(8)
+FG_F32, FG_BF16, FG_F16 = 0, 1, 2
+
+_DTYPES = {torch.float32: FG_F32, torch.bfloat16: FG_BF16, torch.float16: FG_F16}
+
+
+class FgmlError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"fgml status {status}: {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """fg_params; defaults (via ``params()``) are the paper's."""
+
+    _fields_ = [("eps_r", ctypes.c_float), ("omega", ctypes.c_float),
+                ("small_size", ctypes.c_int), ("small_iters", ctypes.c_int),
+                ("big_iters", ctypes.c_int), ("order", ctypes.c_int),
+                ("clamp", ctypes.c_int), ("init", ctypes.c_float)]
+
+
+class Image(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("w", ctypes.c_int), ("h", ctypes.c_int),
+                ("row_pitch_bytes", ctypes.c_longlong), ("dtype", ctypes.c_int)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load():
+    """Loads libfgml.so (built by ``paper_2006_14970_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfgml.so is not built ({path}); run "
+                           "paper_2006_14970_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    ip = P(ctypes.c_int)
+    lib.fg_params_default.argtypes = [P(Params)]
+    lib.fg_params_default.restype = None
+    lib.fg_schedule.argtypes = [ctypes.c_int, ctypes.c_int, P(Params), ip, ip, ip, ctypes.c_int]
+    lib.fg_schedule.restype = ctypes.c_int
+    lib.fg_estimate.argtypes = [P(Image), P(Image), P(Params), P(Image), P(Image), vp]
+    lib.fg_estimate.restype = ctypes.c_int
+    lib.fg_estimate_host.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     P(Params), vp, vp, vp]
+    lib.fg_estimate_host.restype = ctypes.c_int
+    lib.fg_level_pass.argtypes = [P(Image), P(Image), P(Image), P(Image), ctypes.c_int,
+                                  P(Params), P(Image), P(Image), vp]
+    lib.fg_level_pass.restype = ctypes.c_int
+    lib.fg_sync.argtypes = [vp]
+    lib.fg_sync.restype = ctypes.c_int
+    lib.fg_release_workspace.argtypes = [vp]
+    lib.fg_release_workspace.restype = ctypes.c_int
+    lib.fg_last_error.argtypes = []
+    lib.fg_last_error.restype = ctypes.c_char_p
+    lib.fg_version.argtypes = []
+    lib.fg_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/fgml.h declares."""
+    text = open(os.path.join(_build.INCLUDE, "fgml.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fg_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(status: int):
+    if status != FG_OK:
+        raise FgmlError(status, load().fg_last_error().decode())
+
+
+def params(**kw) -> Params:
+    p = Params()
+    load().fg_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, int(v) if k in ("small_size", "small_iters", "big_iters", "order",
+                                      "clamp") else float(v))
+    return p
+
+
+def schedule(w: int, h: int, p: Params | None = None):
+    """Level sizes and sweep counts [(w_l, h_l, k_l)] of Algorithm 1 (host planner)."""
+    cap = 64
+    ws, hs, ks = (ctypes.c_int * cap)(), (ctypes.c_int * cap)(), (ctypes.c_int * cap)()
+    n = load().fg_schedule(int(w), int(h), ctypes.byref(p) if p is not None else None,
+                           ws, hs, ks, cap)
+    if n < 0:
+        raise ValueError(f"invalid size {w}x{h}")
+    return [(ws[i], hs[i], ks[i]) for i in range(n)]
+
+
+def _image(t: torch.Tensor, channels: int, name: str) -> Image:
+    if t.dtype not in _DTYPES:
+        raise TypeError(f"{name}: dtype {t.dtype} is not float32/bfloat16/float16")
+    if channels == 3:
+        if t.dim() != 3 or t.shape[2] != 3 or t.stride(2) != 1 or t.stride(1) != 3:
+            raise ValueError(f"{name} must be [H, W, 3] with packed pixels")
+    else:
+        if t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError(f"{name} must be [H, W] with unit column stride")
+    return Image(t.data_ptr(), t.shape[1], t.shape[0], t.stride(0) * t.element_size(),
+                 _DTYPES[t.dtype])
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def estimate(I: torch.Tensor, alpha: torch.Tensor, p: Params | None = None,
+             F: torch.Tensor | None = None, B: torch.Tensor | None = None, stream=None):
+    """fg_estimate on device tensors I [H, W, 3] and alpha [H, W]; returns (F, B)."""
+    if not (I.is_cuda and alpha.is_cuda):
+        raise ValueError("fg_estimate takes CUDA tensors; use estimate_host for host memory")
+    if F is None:
+        F = torch.empty_like(I, memory_format=torch.contiguous_format)
+    if B is None:
+        B = torch.empty_like(I, memory_format=torch.contiguous_format)
+    iI, iA, iF, iB = _image(I, 3, "I"), _image(alpha, 1, "alpha"), _image(F, 3, "F"), \
+        _image(B, 3, "B")
+    _check(load().fg_estimate(ctypes.byref(iI), ctypes.byref(iA),
+                              ctypes.byref(p) if p is not None else None,
+                              ctypes.byref(iF), ctypes.byref(iB), _stream(stream)))
+    return F, B
+
+
+def estimate_host(I: torch.Tensor, alpha: torch.Tensor, p: Params | None = None,
+                  F: torch.Tensor | None = None, B: torch.Tensor | None = None, stream=None):
+    """fg_estimate_host on contiguous host tensors (pinned for speed); returns (F, B)."""
+    if I.is_cuda or alpha.is_cuda:
+        raise ValueError("estimate_host takes host tensors")
+    I = I.contiguous()
+    alpha = alpha.contiguous()
+    h, w = alpha.shape
+    if I.shape != (h, w, 3) or I.dtype != alpha.dtype or I.dtype not in _DTYPES:
+        raise ValueError("I must be [H, W, 3] and alpha [H, W] of one float dtype")
+    if F is None:
+        F = torch.empty_like(I)
+    if B is None:
+        B = torch.empty_like(I)
+    _check(load().fg_estimate_host(ctypes.c_void_p(I.data_ptr()),
+                                   ctypes.c_void_p(alpha.data_ptr()), w, h, _DTYPES[I.dtype],
+                                   ctypes.byref(p) if p is not None else None,
+                                   ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                   _stream(stream)))
+    return F, B
+
+
+def level_pass(I, alpha, F_src, B_src, iters: int, w: int, h: int, p: Params | None = None,
+               F_dst=None, B_dst=None, stream=None):
+    """fg_level_pass: ``iters`` sweeps of a w x h level from (F_src, B_src)."""
+    if F_dst is None:
+        F_dst = torch.empty((h, w, 3), dtype=I.dtype, device=I.device)
+    if B_dst is None:
+        B_dst = torch.empty((h, w, 3), dtype=I.dtype, device=I.device)
+    imgs = [_image(I, 3, "I"), _image(alpha, 1, "alpha"), _image(F_src, 3, "F_src"),
+            _image(B_src, 3, "B_src"), _image(F_dst, 3, "F_dst"), _image(B_dst, 3, "B_dst")]
+    _check(load().fg_level_pass(*(ctypes.byref(x) for x in imgs[:4]), int(iters),
+                                ctypes.byref(p) if p is not None else None,
+                                ctypes.byref(imgs[4]), ctypes.byref(imgs[5]), _stream(stream)))
+    return F_dst, B_dst
+
+
+def sync(stream=None):
+    _check(load().fg_sync(_stream(stream)))
+
+
+def release_workspace(stream=None):
+    _check(load().fg_release_workspace(_stream(stream)))
+
+
+def version() -> str:
+    return load().fg_version().decode()

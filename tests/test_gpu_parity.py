@@ -1,0 +1,164 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by
+element on the same seeded inputs. Bar: max-abs <= 1e-4 per channel in float32."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2006_14970_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _random_inputs(w, h, seed):
+    rng = np.random.default_rng(seed)
+    if w * h >= 64 * 64:
+        s = synth.make_sample(w, h, seed)
+        return s.I, s.alpha
+    a = rng.random((h, w)).astype(np.float32)
+    a[rng.random((h, w)) < 0.3] = 0.0
+    a[rng.random((h, w)) < 0.3] = 1.0
+    return rng.random((h, w, 3)).astype(np.float32), a
+
+
+def _gpu_ml(fgml, I, a, p=None):
+    F, B = fgml.estimate(_dev(I), _dev(a), p)
+    torch.cuda.synchronize()
+    return F.cpu().numpy().astype(np.float64), B.cpu().numpy().astype(np.float64)
+
+
+def _maxabs(x, y):
+    return [float(np.max(np.abs(x[..., c] - y[..., c]))) for c in range(x.shape[-1])]
+
+
+def _assert_close(F, B, Fo, Bo, tol=TOL, what=""):
+    eF, eB = _maxabs(F, Fo), _maxabs(B, Bo)
+    assert max(eF) <= tol and max(eB) <= tol, f"{what} max-abs F {eF} B {eB}"
+
+
+@pytest.mark.parametrize("name", ["single_128x128", "single_2048x1536_hair"])
+def test_workload_parity(fgml, name):
+    s = synth.workload(name)
+    F, B = _gpu_ml(fgml, s.I, s.alpha)
+    Fo, Bo = oracle.ml(s.I, s.alpha)
+    _assert_close(F, B, Fo, Bo, what=name)
+
+
+SIZES = [(1, 1), (2, 1), (1, 2), (3, 1), (1, 37), (5, 7), (33, 31), (64, 64), (65, 64),
+         (61, 67), (127, 3), (3, 127), (300, 201), (1000, 17), (17, 1000), (4097, 3),
+         (121, 122), (259, 260), (1939, 1192)]
+
+
+@pytest.mark.parametrize("w,h", SIZES)
+def test_ragged_and_degenerate_sizes(fgml, w, h):
+    I, a = _random_inputs(w, h, 1000 + w * 7 + h)
+    F, B = _gpu_ml(fgml, I, a)
+    Fo, Bo = oracle.ml(I, a)
+    _assert_close(F, B, Fo, Bo, what=f"{w}x{h}")
+
+
+@pytest.mark.parametrize("kw", [dict(clamp=0), dict(init=0.5), dict(eps_r=0.02, omega=1.0),
+                                dict(small_iters=3, big_iters=5), dict(big_iters=1),
+                                dict(big_iters=0), dict(small_size=100, small_iters=4),
+                                dict(omega=0.0)])
+def test_parameters(fgml, kw):
+    I, a = _random_inputs(181, 97, 5)
+    p = fgml.params(**kw)
+    F, B = _gpu_ml(fgml, I, a, p)
+    okw = {k: (bool(v) if k == "clamp" else v) for k, v in kw.items()}
+    Fo, Bo = oracle.ml(I, a, oracle.Params(**okw))
+    tol = TOL if kw.get("clamp", 1) else 5e-4
+    _assert_close(F, B, Fo, Bo, tol=tol, what=str(kw))
+
+
+@pytest.mark.parametrize("iters", [0, 1, 2, 3, 4, 7])
+@pytest.mark.parametrize("w,h,sw,sh,Iw,Ih", [(130, 70, 66, 35, 260, 140), (61, 200, 61, 200, 61, 200),
+                                             (500, 9, 251, 5, 1001, 17), (7, 3, 2, 2, 7, 3)])
+def test_level_pass_against_oracle_sweeps(fgml, iters, w, h, sw, sh, Iw, Ih):
+    rng = np.random.default_rng(iters * 100 + w)
+    I = rng.random((Ih, Iw, 3)).astype(np.float32)
+    a = rng.random((Ih, Iw)).astype(np.float32)
+    Fs = rng.random((sh, sw, 3)).astype(np.float32)
+    Bs = rng.random((sh, sw, 3)).astype(np.float32)
+    F, B = fgml.level_pass(_dev(I), _dev(a), _dev(Fs), _dev(Bs), iters, w, h)
+    torch.cuda.synchronize()
+    Il, al = oracle.resize_nearest(I, w, h), oracle.resize_nearest(a, w, h)
+    Fo, Bo = oracle.level_iterate(Il, al, oracle.resize_nearest(Fs, w, h),
+                                  oracle.resize_nearest(Bs, w, h), iters)
+    _assert_close(F.cpu().numpy().astype(np.float64), B.cpu().numpy().astype(np.float64),
+                  Fo, Bo, what=f"iters={iters}")
+
+
+def test_pitched_inputs_and_outputs(fgml):
+    I, a = _random_inputs(203, 150, 9)
+    Ib = torch.zeros((150, 260, 3), device="cuda")
+    Ab = torch.zeros((150, 230), device="cuda")
+    Ib[:, :203] = _dev(I)
+    Ab[:, :203] = _dev(a)
+    Fb = torch.full((150, 211, 3), -7.0, device="cuda")
+    Bb = torch.full((150, 211, 3), -7.0, device="cuda")
+    fgml.estimate(Ib[:, :203], Ab[:, :203], None, Fb[:, :203], Bb[:, :203])
+    torch.cuda.synchronize()
+    Fo, Bo = oracle.ml(I, a)
+    _assert_close(Fb[:, :203].cpu().numpy().astype(np.float64),
+                  Bb[:, :203].cpu().numpy().astype(np.float64), Fo, Bo, what="pitched")
+    # nothing written outside the images
+    assert bool((Fb[:, 203:] == -7.0).all()) and bool((Bb[:, 203:] == -7.0).all())
+
+
+def test_every_output_pixel_is_written(fgml):
+    I, a = _random_inputs(613, 419, 10)
+    F = torch.full((419, 613, 3), float("nan"), device="cuda")
+    B = torch.full((419, 613, 3), float("nan"), device="cuda")
+    fgml.estimate(_dev(I), _dev(a), None, F, B)
+    torch.cuda.synchronize()
+    assert not bool(torch.isnan(F).any()) and not bool(torch.isnan(B).any())
+
+
+def test_exact_invariants_on_gpu(fgml):
+    h, w = 211, 307
+    I = np.full((h, w, 3), 0.37, np.float32)
+    F, B = _gpu_ml(fgml, I, np.ones((h, w), np.float32))
+    assert np.all(B == 0.0) and np.max(np.abs(F - 0.37)) < 1e-6
+    F, B = _gpu_ml(fgml, I, np.zeros((h, w), np.float32))
+    assert np.all(F == 0.0) and np.max(np.abs(B - 0.37)) < 1e-6
+    Ir, ar = _random_inputs(w, h, 11)
+    F, B = _gpu_ml(fgml, Ir, ar)
+    assert F.min() >= 0 and F.max() <= 1 and B.min() >= 0 and B.max() <= 1
+
+
+def test_host_entry_point_matches_device_entry_point(fgml):
+    s = synth.make_sample(517, 389, 12)
+    Fd, Bd = fgml.estimate(_dev(s.I), _dev(s.alpha))
+    torch.cuda.synchronize()
+    Fh, Bh = fgml.estimate_host(torch.from_numpy(s.I).pin_memory(),
+                                torch.from_numpy(s.alpha).pin_memory())
+    assert torch.equal(Fh, Fd.cpu()) and torch.equal(Bh, Bd.cpu())
+
+
+def test_repeated_calls_and_streams_are_deterministic(fgml):
+    s = synth.make_sample(700, 500, 13)
+    I, a = _dev(s.I), _dev(s.alpha)
+    F1, B1 = fgml.estimate(I, a)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        F2, B2 = fgml.estimate(I, a)
+    st.synchronize()
+    torch.cuda.synchronize()
+    F3, B3 = fgml.estimate(I, a)
+    torch.cuda.synchronize()
+    assert torch.equal(F1, F2) and torch.equal(B1, B2)
+    assert torch.equal(F1, F3) and torch.equal(B1, B3)
+
+
+def test_full_size_8k_parity(fgml):
+    s = synth.workload("single_7680x4320")
+    F, B = _gpu_ml(fgml, s.I, s.alpha)
+    Fo, Bo = oracle.ml(s.I, s.alpha)
+    _assert_close(F, B, Fo, Bo, what="7680x4320")
