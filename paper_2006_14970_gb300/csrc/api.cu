@@ -515,3 +515,138 @@ const char *fg_last_error(void) { return g_err.c_str(); }
 const char *fg_version(void) { return "fgml 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ====================================================== no-allocation variant
+//
+// fg_estimate_noalloc runs the same kernels as fg_estimate, but its intermediate pyramid
+// levels live in a fixed array compiled into the library instead of a workspace taken
+// with cudaMalloc. It serves callers that must not allocate device memory from inside
+// this library: processes whose device memory is fully reserved up front by their own
+// pool or budget, and hot loops that cannot afford cudaMalloc's implicit device-wide
+// synchronisation. The array exists once per device that loads the library and stays
+// allocated until the process exits.
+
+namespace {
+
+// Two level buffers of 32 MiB each: room for every intermediate level of an FP32 image
+// of up to about 5.6 megapixels with the default schedule (twice that in BF16/FP16).
+constexpr size_t kNoAllocScratchBytes = 64ull << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[64] = {};
+
+// Device address of the scratch array on the current device. The host-side symbol is
+// only a stand-in, so the address is looked up once per device (with that device
+// current) and cached.
+fg_status noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(FG_ERR_UNSUPPORTED, "device index %d above 63", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the scratch array");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return FG_OK;
+}
+
+}  // namespace
+
+extern "C" fg_status fg_estimate_noalloc(const fg_image *I, const fg_image *alpha,
+                                         const fg_params *params, fg_image *F, fg_image *B,
+                                         void *stream) {
+    g_err.clear();
+    fg_status st;
+    if ((st = check_image(I, 3, "I")) != FG_OK) return st;
+    if ((st = check_image(alpha, 1, "alpha")) != FG_OK) return st;
+    if ((st = check_image(F, 3, "F")) != FG_OK) return st;
+    if ((st = check_image(B, 3, "B")) != FG_OK) return st;
+    const fg_params p = params_or_default(params);
+    if ((st = check_params(p)) != FG_OK) return st;
+    if (alpha->w != I->w || alpha->h != I->h || F->w != I->w || F->h != I->h ||
+        B->w != I->w || B->h != I->h)
+        return fail(FG_ERR_INVALID_ARG, "I, alpha, F and B must have the same size");
+    if (alpha->dtype != I->dtype || F->dtype != I->dtype || B->dtype != I->dtype)
+        return fail(FG_ERR_INVALID_ARG, "I, alpha, F and B must have the same dtype");
+    if (F->row_pitch_bytes != B->row_pitch_bytes)
+        return fail(FG_ERR_INVALID_ARG, "F and B must have the same row pitch");
+    if (overlap(F, 3, B, 3) || overlap(F, 3, I, 3) || overlap(F, 3, alpha, 1) ||
+        overlap(B, 3, I, 3) || overlap(B, 3, alpha, 1))
+        return fail(FG_ERR_INVALID_ARG, "outputs overlap each other or the inputs");
+
+    const int dtype = (int)I->dtype;
+    const int es = elem_size(I->dtype);
+    const Input in{I->ptr, alpha->ptr, I->row_pitch_bytes / es, alpha->row_pitch_bytes / es,
+                   I->w, I->h};
+    const std::vector<Level> lv = plan_levels(in.w, in.h, p);
+    const int n = (int)lv.size();
+    int nc = 0;
+    while (nc < n && nc < kCoarseMaxLevels && (long long)lv[nc].w * lv[nc].h <= kCoarseCap) ++nc;
+    size_t need = 0;   // bytes of one level buffer
+    if (nc < n) need = state_bytes(lv[nc - 1].w, lv[nc - 1].h, es);
+    for (int l = nc; l < n; ++l)
+        if (l != n - 1 || split_sweeps(lv[l].k).size() > 1)
+            need = std::max(need, state_bytes(lv[l].w, lv[l].h, es));
+    if (need > kNoAllocScratchBytes / 2)
+        return fail(FG_ERR_INVALID_ARG,
+                    "%dx%d needs two %zu-byte level buffers; the no-allocation scratch holds "
+                    "two of %zu bytes (use fg_estimate)",
+                    in.w, in.h, need, kNoAllocScratchBytes / 2);
+
+    void *scratch = nullptr;
+    if ((st = noalloc_scratch(&scratch)) != FG_OK) return st;
+    // Every byte a kernel reads from the scratch was written earlier in this call, so
+    // nothing needs clearing between calls.
+    Workspace ws;
+    ws.lev[0].p = scratch;
+    ws.lev[0].bytes = kNoAllocScratchBytes / 2;
+    ws.lev[1].p = (char *)scratch + kNoAllocScratchBytes / 2;
+    ws.lev[1].bytes = kNoAllocScratchBytes / 2;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *Fd = F->ptr, *Bd = B->ptr;
+    const long long d_pitch = F->row_pitch_bytes / es;
+
+    CoarseArgs ca;
+    std::memset(&ca, 0, sizeof ca);
+    ca.I = in.I;
+    ca.I_pitch = in.I_pitch;
+    ca.A = in.A;
+    ca.A_pitch = in.A_pitch;
+    ca.Iw = in.w;
+    ca.Ih = in.h;
+    ca.nlev = nc;
+    for (int l = 0; l < nc; ++l) {
+        ca.lw[l] = lv[l].w;
+        ca.lh[l] = lv[l].h;
+        ca.lk[l] = lv[l].k;
+    }
+    ca.eps = p.eps_r;
+    ca.omega = p.omega;
+    ca.init = p.init;
+    State src{};
+    int buf = -1;
+    if (nc == n) {
+        ca.Fd = Fd;
+        ca.Bd = Bd;
+        ca.d_pitch = d_pitch;
+    } else {
+        src = state_in(ws.lev[0], lv[nc - 1].w, lv[nc - 1].h, es);
+        buf = 0;
+        ca.Fd = (void *)src.F;
+        ca.Bd = (void *)src.B;
+        ca.d_pitch = src.pitch;
+    }
+    cudaError_t e = launch_coarse(dtype, p.clamp, ca, s);
+    if (e != cudaSuccess) return cuda_fail(e, "coarse kernel launch");
+    for (int l = nc; l < n; ++l) {
+        st = run_level(dtype, p, in, src, buf, lv[l].k, lv[l].w, lv[l].h, l == n - 1, Fd, Bd,
+                       d_pitch, ws, es, s);
+        if (st != FG_OK) return st;
+    }
+    return FG_OK;
+}

@@ -202,3 +202,25 @@ def release_workspace(stream=None):
 
 def version() -> str:
     return load().fg_version().decode()
+
+
+def estimate_noalloc(I: torch.Tensor, alpha: torch.Tensor, p: Params | None = None,
+                     F: torch.Tensor | None = None, B: torch.Tensor | None = None, stream=None):
+    """fg_estimate_noalloc: as ``estimate`` but the library allocates no device memory
+    (intermediate levels use its fixed 64 MiB array; larger images are rejected). For
+    callers that cannot let the library call cudaMalloc. Calls that overlap on the GPU
+    share that array and race; keep them on one stream."""
+    lib = load()
+    fn = lib.fg_estimate_noalloc
+    P = ctypes.POINTER
+    fn.argtypes = [P(Image), P(Image), P(Params), P(Image), P(Image), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    if F is None:
+        F = torch.empty_like(I, memory_format=torch.contiguous_format)
+    if B is None:
+        B = torch.empty_like(I, memory_format=torch.contiguous_format)
+    iI, iA, iF, iB = _image(I, 3, "I"), _image(alpha, 1, "alpha"), _image(F, 3, "F"), \
+        _image(B, 3, "B")
+    _check(fn(ctypes.byref(iI), ctypes.byref(iA), ctypes.byref(p) if p is not None else None,
+              ctypes.byref(iF), ctypes.byref(iB), _stream(stream)))
+    return F, B
