@@ -62,6 +62,20 @@ struct Level {
     int w, h, k;
 };
 
+// Levels 1..nc run in the one-block coarse kernel: the longest prefix of levels with at
+// most kCoarseCap pixels each and kCoarseTotal together (level 1 is at most 2 x 2).
+int coarse_levels(const std::vector<Level> &lv) {
+    int nc = 0;
+    long long total = 0;
+    while (nc < (int)lv.size() && nc < kCoarseMaxLevels) {
+        const long long n = (long long)lv[nc].w * lv[nc].h;
+        if (n > kCoarseCap || total + n > kCoarseTotal) break;
+        total += n;
+        ++nc;
+    }
+    return nc;
+}
+
 std::vector<Level> plan_levels(int w, int h, const fg_params &p) {
     const int n = level_count(w, h);
     std::vector<Level> lv(n);
@@ -208,6 +222,9 @@ struct Input {
     int w, h;
 };
 
+// Shared memory of one ring-variant block; two blocks must fit on an SM.
+constexpr size_t kRingSmemBudget = 110 * 1024;
+
 // Rows per warp of a level pass: enough warps for several waves of resident warps.
 int strip_rows(int w, int h) {
     const int nx = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
@@ -243,6 +260,19 @@ cudaError_t pass(int dtype, int iters, int clamp, const fg_params &p, const Inpu
     a.strip_h = strip_rows(w, h);
     a.n_xstrips = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
     a.n_warps = a.n_xstrips * ((h + a.strip_h - 1) / a.strip_h);
+    a.capI = a.capA = a.capS = a.slot_bytes = 0;
+    if (iters == 1 || iters == 2) {
+        // ring slots: each segment's 16-byte aligned superset (up to 30 extra bytes)
+        const int es = dtype == kF32 ? 4 : 2;
+        auto r16 = [](int v) { return (v + 15) & ~15; };
+        const int spanI = strip_span(in.w, w), spanS = strip_span(src.w, w);
+        a.capI = r16(3 * spanI * es + 30);
+        a.capA = r16(spanI * es + 30);
+        a.capS = r16(3 * spanS * es + 30);
+        a.slot_bytes = a.capI + a.capA + 2 * a.capS;
+        if (level_pass_ring_smem(a.slot_bytes) <= kRingSmemBudget)
+            return launch_level_pass_ring(dtype, iters, clamp, a, s);
+    }
     return launch_level_pass(dtype, iters, clamp, a, s);
 }
 
@@ -288,8 +318,7 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
     const int es = dtype == kF32 ? 4 : 2;
     const std::vector<Level> lv = plan_levels(in.w, in.h, p);
     const int n = (int)lv.size();
-    int nc = 0;   // levels run by the coarse kernel
-    while (nc < n && nc < kCoarseMaxLevels && (long long)lv[nc].w * lv[nc].h <= kCoarseCap) ++nc;
+    const int nc = coarse_levels(lv);   // levels run by the coarse kernel
 
     // workspace: every intermediate state, including extra passes of the top level
     size_t need = 0;
@@ -320,6 +349,8 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
         ca.lw[l] = lv[l].w;
         ca.lh[l] = lv[l].h;
         ca.lk[l] = lv[l].k;
+        ca.off[l] = ca.total;
+        ca.total += lv[l].w * lv[l].h;
     }
     ca.eps = p.eps_r;
     ca.omega = p.omega;
@@ -490,6 +521,10 @@ fg_status fg_level_pass(const fg_image *I, const fg_image *alpha, const fg_image
 fg_status fg_sync(void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    int code = 0;
+    e = read_and_clear_device_error(&code, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    if (code) return fail(FG_ERR_TIMEOUT, "a bounded device-side wait gave up (code %d)", code);
     return FG_OK;
 }
 
@@ -585,8 +620,7 @@ extern "C" fg_status fg_estimate_noalloc(const fg_image *I, const fg_image *alph
                    I->w, I->h};
     const std::vector<Level> lv = plan_levels(in.w, in.h, p);
     const int n = (int)lv.size();
-    int nc = 0;
-    while (nc < n && nc < kCoarseMaxLevels && (long long)lv[nc].w * lv[nc].h <= kCoarseCap) ++nc;
+    const int nc = coarse_levels(lv);
     size_t need = 0;   // bytes of one level buffer
     if (nc < n) need = state_bytes(lv[nc - 1].w, lv[nc - 1].h, es);
     for (int l = nc; l < n; ++l)
@@ -624,6 +658,8 @@ extern "C" fg_status fg_estimate_noalloc(const fg_image *I, const fg_image *alph
         ca.lw[l] = lv[l].w;
         ca.lh[l] = lv[l].h;
         ca.lk[l] = lv[l].k;
+        ca.off[l] = ca.total;
+        ca.total += lv[l].w * lv[l].h;
     }
     ca.eps = p.eps_r;
     ca.omega = p.omega;

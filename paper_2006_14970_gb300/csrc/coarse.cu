@@ -1,11 +1,14 @@
-// Coarse levels: every level whose F and B fit in one SM's shared memory runs inside
-// one persistent 1024-thread block, from the 1x1 start of Algorithm 1 up to level
-// `nlev`. Only the level's I values and alpha come from HBM (nearest resize of the
-// full-resolution input, Algorithm 1); the starting F and B of a level are the nearest
-// resize of the previous level, done shared memory to shared memory, and the sweeps
-// (10 per small level, Section III-D) ping-pong between two shared buffers with a block
-// barrier per Jacobi sweep. The per-pixel solve is the closed form of Section III-C,
-// as in the level-pass kernel, in scalar float32.
+// Coarse levels: every level of at most 1024 pixels (with the paper's schedule, all
+// the 10-sweep levels up to 32 x 32, Section III-D) runs inside one persistent
+// 1024-thread block, one pixel per thread, from the 1x1 start of Algorithm 1 up to level
+// `nlev`.
+//  - I_l and alpha_l of every coarse level are gathered from the full-resolution input
+//    (nearest resize, Algorithm 1) in one burst at the start, so HBM latency is paid once.
+//  - F and B live in shared memory as (F, B) pairs per channel, ping-ponged between two
+//    buffers, with one block barrier per Jacobi sweep.
+//  - Each thread forms its pixel's neighbour weights and the inverse of its 2x2 matrix
+//    (Section III-C) once per level; a sweep is then 4 neighbour reads, packed
+//    multiply-adds and the clamped solve (Algorithm 1).
 #include "fgml_internal.h"
 
 namespace fgml {
@@ -13,83 +16,99 @@ namespace {
 
 constexpr int kThreads = 1024;
 
-// Shared memory: two F/B buffers (6 planes each), alpha, and a packed (row, column)
-// source index of I per pixel.
-constexpr size_t kSmemBytes = (size_t)kCoarseCap * (13 * sizeof(float) + sizeof(int));
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 
 template <typename T, bool CLAMP>
 __global__ void __launch_bounds__(kThreads, 1) coarse_kernel(const CoarseArgs p) {
-    extern __shared__ float sm[];
-    float *bufA = sm;
-    float *bufB = sm + 6 * kCoarseCap;
-    float *al = sm + 12 * kCoarseCap;
-    int *isrc = reinterpret_cast<int *>(sm + 13 * kCoarseCap);
+    extern __shared__ __align__(16) float sm[];
+    // [0, 3 * kCoarseCap) float2: buffer X; then buffer Y; then per level I (3 floats per
+    // pixel) and alpha, at the offsets p.off[l] (in pixels)
+    float2 *bufX = reinterpret_cast<float2 *>(sm);
+    float2 *bufY = bufX + 3 * kCoarseCap;
+    float *Ilv = reinterpret_cast<float *>(bufY + 3 * kCoarseCap);
+    float *Alv = Ilv + 3 * p.total;
     const T *I = static_cast<const T *>(p.I);
     const T *A = static_cast<const T *>(p.A);
     const int tid = threadIdx.x;
 
-    float *cur = bufA, *nxt = bufB;
-    if (tid < 6) cur[tid * kCoarseCap] = p.init;     // F, B <- init at 1 x 1
-    int pw = 1, ph = 1;
-    __syncthreads();
-
+    // gather I_l and alpha_l of all coarse levels
     for (int l = 0; l < p.nlev; ++l) {
-        const int w = p.lw[l], h = p.lh[l], k = p.lk[l], n = w * h;
-        // resize: alpha and the I source index from the full-resolution input,
-        // F and B from the previous level
+        const int w = p.lw[l], h = p.lh[l], n = w * h, o = p.off[l];
         for (int i = tid; i < n; i += kThreads) {
             const int x = i % w, y = i / w;
             const int gx = nearest_src(x, p.Iw, w), gy = nearest_src(y, p.Ih, h);
-            isrc[i] = (gy << 16) | gx;
-            al[i] = ld_elem(A + (long long)gy * p.A_pitch + gx);
+            const T *Ip = I + (long long)gy * p.I_pitch + 3 * gx;
+            Ilv[3 * (o + i) + 0] = ld_elem(Ip + 0);
+            Ilv[3 * (o + i) + 1] = ld_elem(Ip + 1);
+            Ilv[3 * (o + i) + 2] = ld_elem(Ip + 2);
+            Alv[o + i] = ld_elem(A + (long long)gy * p.A_pitch + gx);
+        }
+    }
+    float2 *cur = bufX, *nxt = bufY;
+    if (tid == 0)
+        for (int c = 0; c < 3; ++c) cur[c * kCoarseCap] = f2(p.init, p.init);   // 1 x 1 start
+    __syncthreads();
+
+    int pw = 1, ph = 1;
+    for (int l = 0; l < p.nlev; ++l) {
+        const int w = p.lw[l], h = p.lh[l], k = p.lk[l], n = w * h, o = p.off[l];
+        const bool mine = tid < n;
+        const int x = mine ? tid % w : 0, y = mine ? tid / w : 0;
+        // starting F, B: nearest resize of the previous level
+        if (mine) {
             const int q = nearest_src(y, ph, h) * pw + nearest_src(x, pw, w);
 #pragma unroll
-            for (int c = 0; c < 6; ++c) nxt[c * kCoarseCap + i] = cur[c * kCoarseCap + q];
+            for (int c = 0; c < 3; ++c) nxt[c * kCoarseCap + tid] = cur[c * kCoarseCap + q];
+        }
+        // neighbours clamped onto the level (Algorithm 1), their weights and A^{-1}
+        int nb[4] = {0, 0, 0, 0};
+        float wj[4] = {0.f, 0.f, 0.f, 0.f};
+        float ai = 0.f, be = 0.f, mFF = 0.f, mBB = 0.f, nFB = 0.f, Ic[3] = {0.f, 0.f, 0.f};
+        if (mine) {
+            nb[0] = y * w + max(x - 1, 0);
+            nb[1] = y * w + min(x + 1, w - 1);
+            nb[2] = max(y - 1, 0) * w + x;
+            nb[3] = min(y + 1, h - 1) * w + x;
+            ai = Alv[o + tid];
+            be = 1.f - ai;
+            float S = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                wj[j] = fmaf(p.omega, fabsf(ai - Alv[o + nb[j]]), p.eps);
+                S += wj[j];
+            }
+            const float A00 = fmaf(ai, ai, S), A11 = fmaf(be, be, S), A01 = ai * be;
+            const float m = __fdividef(1.f, fmaf(A00, A11, -A01 * A01));
+            mFF = A11 * m;
+            mBB = A00 * m;
+            nFB = -A01 * m;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Ic[c] = Ilv[3 * (o + tid) + c];
         }
         __syncthreads();
-        { float *t = cur; cur = nxt; nxt = t; }
+        { float2 *t = cur; cur = nxt; nxt = t; }
 
         for (int it = 0; it < k; ++it) {
-            for (int i = tid; i < n; i += kThreads) {
-                const int x = i % w, y = i / w;
-                const float ai = al[i];
-                // the 4 neighbours, clamped onto the image (Algorithm 1)
-                const int nb[4] = {y * w + max(x - 1, 0), y * w + min(x + 1, w - 1),
-                                   max(y - 1, 0) * w + x, min(y + 1, h - 1) * w + x};
-                float S = 0.f;
-                float sF[3] = {0.f, 0.f, 0.f}, sB[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int q = nb[j];
-                    const float d = fmaf(p.omega, fabsf(ai - al[q]), p.eps);
-                    S += d;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        sF[c] = fmaf(d, cur[c * kCoarseCap + q], sF[c]);
-                        sB[c] = fmaf(d, cur[(3 + c) * kCoarseCap + q], sB[c]);
-                    }
-                }
-                const int src = isrc[i];
-                const T *Ip = I + (long long)(src >> 16) * p.I_pitch + 3 * (src & 0xffff);
-                const float be = 1.f - ai;
-                const float A00 = fmaf(ai, ai, S), A11 = fmaf(be, be, S), A01 = ai * be;
-                const float m = __frcp_rn(fmaf(A00, A11, -A01 * A01));
+            if (mine) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float Ic = ld_elem(Ip + c);
-                    const float bF = fmaf(ai, Ic, sF[c]), bB = fmaf(be, Ic, sB[c]);
-                    float gF = (A11 * bF - A01 * bB) * m;
-                    float gB = (A00 * bB - A01 * bF) * m;
+                    // (sum s_j F_j, sum s_j B_j) as one packed pair
+                    float2 s = __fmul2_rn(f2(wj[0], wj[0]), cur[c * kCoarseCap + nb[0]]);
+#pragma unroll
+                    for (int j = 1; j < 4; ++j)
+                        s = __ffma2_rn(f2(wj[j], wj[j]), cur[c * kCoarseCap + nb[j]], s);
+                    const float bF = fmaf(ai, Ic[c], s.x), bB = fmaf(be, Ic[c], s.y);
+                    float gF = fmaf(mFF, bF, nFB * bB);
+                    float gB = fmaf(mBB, bB, nFB * bF);
                     if (CLAMP) {
                         gF = __saturatef(gF);
                         gB = __saturatef(gB);
                     }
-                    nxt[c * kCoarseCap + i] = gF;
-                    nxt[(3 + c) * kCoarseCap + i] = gB;
+                    nxt[c * kCoarseCap + tid] = f2(gF, gB);
                 }
             }
             __syncthreads();
-            { float *t = cur; cur = nxt; nxt = t; }
+            { float2 *t = cur; cur = nxt; nxt = t; }
         }
         pw = w;
         ph = h;
@@ -97,31 +116,35 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_kernel(const CoarseArgs p)
 
     T *F = static_cast<T *>(p.Fd);
     T *B = static_cast<T *>(p.Bd);
-    for (int i = tid; i < pw * ph; i += kThreads) {
-        const int x = i % pw, y = i / pw;
+    if (tid < pw * ph) {
+        const int x = tid % pw, y = tid / pw;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            st_elem(F + (long long)y * p.d_pitch + 3 * x + c, cur[c * kCoarseCap + i]);
-            st_elem(B + (long long)y * p.d_pitch + 3 * x + c, cur[(3 + c) * kCoarseCap + i]);
+            const float2 v = cur[c * kCoarseCap + tid];
+            st_elem(F + (long long)y * p.d_pitch + 3 * x + c, v.x);
+            st_elem(B + (long long)y * p.d_pitch + 3 * x + c, v.y);
         }
     }
 }
 
 template <typename T, bool CLAMP>
 cudaError_t launch_t(const CoarseArgs &a, cudaStream_t s) {
+    const size_t smem = coarse_smem_bytes(a.total);
     cudaError_t e = cudaFuncSetAttribute(coarse_kernel<T, CLAMP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    coarse_kernel<T, CLAMP><<<1, kThreads, kSmemBytes, s>>>(a);
+    coarse_kernel<T, CLAMP><<<1, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t coarse_smem_bytes() { return kSmemBytes; }
+size_t coarse_smem_bytes(int total_pixels) {
+    return 2 * 3 * kCoarseCap * sizeof(float2) + (size_t)total_pixels * 4 * sizeof(float);
+}
 
 cudaError_t launch_coarse(int dtype, int clamp, const CoarseArgs &a, cudaStream_t s) {
+    if (a.nlev < 1 || a.nlev > kCoarseMaxLevels || a.total > kCoarseTotal) return cudaErrorInvalidValue;
     switch (dtype) {
         case kF32: return clamp ? launch_t<float, true>(a, s) : launch_t<float, false>(a, s);
         case kBF16:

@@ -52,10 +52,19 @@ struct PassArgs {
     int strip_h;            // output rows per warp
     int n_xstrips;          // strips of 60 output columns
     int n_warps;            // n_xstrips * ceil(h / strip_h)
+    // row-ring variant only: bytes of each segment of a ring slot (multiples of 16)
+    int capI, capA, capS, slot_bytes;
 };
 
-constexpr int kCoarseCap = 4096;   // pixels of the largest level the one-block kernel holds
+// Largest source-column span (in pixels) of one warp strip of a level pass, for a gather
+// from a side of length S to a level side of length D (host planning of ring slots).
+int strip_span(int S, int D);
+// Per-warp ring slots of the row-ring level pass.
+constexpr int kRingSlots = 6;
+
+constexpr int kCoarseCap = 1024;     // pixels of the largest level the one-block kernel runs
 constexpr int kCoarseMaxLevels = 16;
+constexpr int kCoarseTotal = 8192;   // pixels of all its levels together
 
 struct CoarseArgs {
     const void *I;
@@ -65,6 +74,8 @@ struct CoarseArgs {
     int Iw, Ih;
     int nlev;                              // levels 1..nlev run in the block
     int lw[kCoarseMaxLevels], lh[kCoarseMaxLevels], lk[kCoarseMaxLevels];
+    int off[kCoarseMaxLevels];             // first pixel of each level in the gathered I/alpha
+    int total;                             // pixels of all nlev levels
     void *Fd, *Bd;                         // F and B of level nlev
     long long d_pitch;
     float eps, omega, init;
@@ -75,7 +86,14 @@ enum DType { kF32 = 0, kBF16 = 1, kF16 = 2 };
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_level_pass(int dtype, int iters, int clamp, const PassArgs &a,
                               cudaStream_t s);
+// Ring variant (TMA bulk row copies into a per-warp shared-memory ring): a.cap*/slot_bytes
+// must be filled in; returns cudaErrorInvalidValue if iters is not 1 or 2.
+cudaError_t launch_level_pass_ring(int dtype, int iters, int clamp, const PassArgs &a,
+                                   cudaStream_t s);
+size_t level_pass_ring_smem(int slot_bytes);
+// Device error word of the library's bounded waits (0 = no error).
+cudaError_t read_and_clear_device_error(int *code, cudaStream_t s);
 cudaError_t launch_coarse(int dtype, int clamp, const CoarseArgs &a, cudaStream_t s);
-size_t coarse_smem_bytes();
+size_t coarse_smem_bytes(int total_pixels);
 
 }  // namespace fgml

@@ -1,30 +1,45 @@
 // Level pass: K Jacobi sweeps of one pyramid level in a single trip through HBM.
 //
 // Each warp owns a strip of 64 columns (two adjacent pixels per lane) and walks down
-// its rows. Row r of the starting state is gathered from HBM exactly once (alpha and I
-// by nearest resize of the full-resolution input, F and B by nearest resize of the
-// previous level, Algorithm 1), sweep 1 is computed one row behind the loads and sweep 2
+// its rows. Row r of the starting state is read from HBM exactly once (alpha and I by
+// nearest resize of the full-resolution input, F and B by nearest resize of the
+// previous level, Algorithm 1); sweep 1 is computed one row behind the loads and sweep 2
 // one row behind sweep 1, all in registers: three-row register queues per sweep, left
 // and right neighbours through warp shuffles. The two outermost columns of the strip
 // are halo, so a warp writes 60 columns; the strip's vertical halo is K rows.
+//
+// Rows reach the warp in one of two ways:
+//  - ring variant (the fast path): a per-warp ring of kRingSlots row slots in shared
+//    memory, filled by bulk asynchronous copies (the TMA engine, one elected lane, one
+//    copy per image segment) that run several rows ahead; completion is tracked by one
+//    mbarrier per slot, and every wait is bounded;
+//  - register variant: plain loads one row ahead into registers (used when a strip's
+//    source span is too wide for the ring, and for zero-sweep levels).
 //
 // The per-pixel update is the closed-form 2x2 solve of Section III-C,
 //   g = (U U^T + S I_2)^{-1} (U I + sum_j s_j [F_j; B_j]),  U = (alpha, 1 - alpha),
 // with s_j = eps_r + omega |alpha_i - alpha_j| over the 4-neighbourhood and S = sum s_j,
 // solved through the adjugate and clamped to [0, 1] (Algorithm 1). A neighbour outside
 // the image is the pixel itself (Algorithm 1 clamps coordinates): its weight is eps_r
-// and its value the pixel's own previous value. Pairs of pixels use the packed
+// and its value the pixel's own previous value. The matrix depends only on alpha, so its
+// inverse is formed once per row and used by both sweeps. Pairs of pixels use the packed
 // float32x2 arithmetic of sm_100-class GPUs.
 #include "fgml_internal.h"
 
 #include <algorithm>
 
 namespace fgml {
+
+// Set by a kernel whose bounded wait gave up (1 = an mbarrier wait timed out).
+__device__ int g_device_error;
+
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kStripW = 60;          // output columns per warp
 constexpr int kWarpsPerBlock = 4;
+constexpr int kLaneCols = 64;        // columns held by a warp (2 per lane)
+constexpr long long kWaitLimit = 1LL << 22;   // try_wait polls before a wait gives up
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -41,9 +56,10 @@ struct RowK {               // per-row data of a lane's pixel pair
     float2 I[3];            // image
     float2 wl, wr, wu, wd;  // weights of the left/right/up/down neighbour, 0 if clamped
     float2 ws;              // eps_r per clamped neighbour (weight of the pixel's own value)
+    float2 mFF, mBB, nFB;   // A^{-1} = [[mFF, -nFB'], ...]: F' = mFF bF + nFB bB etc.
 };
 
-struct Raw {                // one row as loaded
+struct Raw {                // one row as read
     float a0, a1;
     float i0[3], i1[3];
     float f0[3], f1[3], b0[3], b1[3];
@@ -51,32 +67,10 @@ struct Raw {                // one row as loaded
 
 struct LaneGeo {
     int x;                  // column of the lane's first pixel (may be outside the image)
-    int oi0, oi1;           // element offsets of the two pixels in a row of I
-    int oa0, oa1;           // ... in a row of alpha
-    int os0, os1;           // ... in a row of the starting F and B
+    int gi0, gi1;           // source columns of the two pixels in I and alpha
+    int gs0, gs1;           // source columns in the starting F and B
     bool inL0, inR0, inR1;  // left of p0, right of p0, right of p1 lie inside the image
 };
-
-template <typename T>
-__device__ __forceinline__ void load_raw(const PassArgs &p, const LaneGeo &g, int r, Raw &o) {
-    const int gy = nearest_src(r, p.Ih, p.h);
-    const int sy = nearest_src(r, p.sh, p.h);
-    const T *Ir = static_cast<const T *>(p.I) + (long long)gy * p.I_pitch;
-    const T *Ar = static_cast<const T *>(p.A) + (long long)gy * p.A_pitch;
-    const T *Fr = static_cast<const T *>(p.Fs) + (long long)sy * p.s_pitch;
-    const T *Br = static_cast<const T *>(p.Bs) + (long long)sy * p.s_pitch;
-    o.a0 = ld_elem(Ar + g.oa0);
-    o.a1 = ld_elem(Ar + g.oa1);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        o.i0[c] = ld_elem(Ir + g.oi0 + c);
-        o.i1[c] = ld_elem(Ir + g.oi1 + c);
-        o.f0[c] = ld_elem(Fr + g.os0 + c);
-        o.f1[c] = ld_elem(Fr + g.os1 + c);
-        o.b0[c] = ld_elem(Br + g.os0 + c);
-        o.b1[c] = ld_elem(Br + g.os1 + c);
-    }
-}
 
 __device__ __forceinline__ float edge_w(float ai, float aj, float eps, float omega) {
     return fmaf(omega, fabsf(ai - aj), eps);
@@ -113,45 +107,51 @@ __device__ __forceinline__ void make_row(const Raw &raw, const LaneGeo &g, int r
     k.wd = f2(0.f, 0.f);
 }
 
+// Row q's weights are complete (its down weight is known): form A^{-1} once.
+// A = [[alpha^2 + S, alpha(1-alpha)], [alpha(1-alpha), (1-alpha)^2 + S]].
+__device__ __forceinline__ void finish_row(RowK &k) {
+    const float2 S = add2(add2(add2(k.wl, k.wr), add2(k.wu, k.wd)), k.ws);
+    const float2 be = f2(1.f - k.a.x, 1.f - k.a.y);
+    const float2 A00 = fma2(k.a, k.a, S);
+    const float2 A11 = fma2(be, be, S);
+    const float2 A01 = mul2(k.a, be);
+    const float2 det = fma2(A00, A11, neg2(mul2(A01, A01)));
+    const float2 m = f2(__fdividef(1.f, det.x), __fdividef(1.f, det.y));
+    k.mFF = mul2(A11, m);
+    k.mBB = mul2(A00, m);
+    k.nFB = neg2(mul2(A01, m));
+}
+
 // One Jacobi update of a row: c = the row's previous state, up/dn = the previous state
 // of the rows above and below (ignored where the weight is 0).
 template <bool CLAMP>
 __device__ __forceinline__ void update(const RowK &k, const FB &c, const FB &up, const FB &dn,
                                        FB &out) {
-    const float2 S = add2(add2(add2(k.wl, k.wr), add2(k.wu, k.wd)), k.ws);
-    const float2 be = f2(1.f - k.a.x, 1.f - k.a.y);           // 1 - alpha
-    const float2 A00 = fma2(k.a, k.a, S);                      // alpha^2 + S
-    const float2 A11 = fma2(be, be, S);                        // (1 - alpha)^2 + S
-    const float2 A01 = mul2(k.a, be);                          // alpha (1 - alpha)
-    const float2 det = fma2(A00, A11, neg2(mul2(A01, A01)));
-    const float2 m = f2(__frcp_rn(det.x), __frcp_rn(det.y));
-    const float2 mFF = mul2(A11, m), mBB = mul2(A00, m), nFB = neg2(mul2(A01, m));
+    const float2 be = f2(1.f - k.a.x, 1.f - k.a.y);
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         const float lF = __shfl_up_sync(kFull, c.F[ch].y, 1);
         const float rF = __shfl_down_sync(kFull, c.F[ch].x, 1);
         const float lB = __shfl_up_sync(kFull, c.B[ch].y, 1);
         const float rB = __shfl_down_sync(kFull, c.B[ch].x, 1);
-        float2 sF = mul2(k.ws, c.F[ch]);
+        float2 sF = fma2(k.ws, c.F[ch], mul2(k.wu, up.F[ch]));
         sF = fma2(k.wl, f2(lF, c.F[ch].x), sF);
         sF = fma2(k.wr, f2(c.F[ch].y, rF), sF);
-        sF = fma2(k.wu, up.F[ch], sF);
         sF = fma2(k.wd, dn.F[ch], sF);
-        float2 sB = mul2(k.ws, c.B[ch]);
+        float2 sB = fma2(k.ws, c.B[ch], mul2(k.wu, up.B[ch]));
         sB = fma2(k.wl, f2(lB, c.B[ch].x), sB);
         sB = fma2(k.wr, f2(c.B[ch].y, rB), sB);
-        sB = fma2(k.wu, up.B[ch], sB);
         sB = fma2(k.wd, dn.B[ch], sB);
         const float2 bF = fma2(k.a, k.I[ch], sF);              // alpha I + sum s_j F_j
         const float2 bB = fma2(be, k.I[ch], sB);               // (1-alpha) I + sum s_j B_j
-        const float2 tF = mul2(nFB, bB);
-        const float2 tB = mul2(nFB, bF);
+        const float2 tF = mul2(k.nFB, bB);
+        const float2 tB = mul2(k.nFB, bF);
         if (CLAMP) {
-            out.F[ch] = f2(__saturatef(fmaf(mFF.x, bF.x, tF.x)), __saturatef(fmaf(mFF.y, bF.y, tF.y)));
-            out.B[ch] = f2(__saturatef(fmaf(mBB.x, bB.x, tB.x)), __saturatef(fmaf(mBB.y, bB.y, tB.y)));
+            out.F[ch] = f2(__saturatef(fmaf(k.mFF.x, bF.x, tF.x)), __saturatef(fmaf(k.mFF.y, bF.y, tF.y)));
+            out.B[ch] = f2(__saturatef(fmaf(k.mBB.x, bB.x, tB.x)), __saturatef(fmaf(k.mBB.y, bB.y, tB.y)));
         } else {
-            out.F[ch] = fma2(mFF, bF, tF);
-            out.B[ch] = fma2(mBB, bB, tB);
+            out.F[ch] = fma2(k.mFF, bF, tF);
+            out.B[ch] = fma2(k.mBB, bB, tB);
         }
     }
 }
@@ -161,6 +161,17 @@ __device__ __forceinline__ void store_row(const PassArgs &p, const LaneGeo &g, i
                                           const FB &v, bool o0, bool o1) {
     T *Fr = static_cast<T *>(p.Fd) + (long long)r * p.d_pitch + 3 * g.x;
     T *Br = static_cast<T *>(p.Bd) + (long long)r * p.d_pitch + 3 * g.x;
+    if (sizeof(T) == 4 && o0 && o1 && ((reinterpret_cast<uintptr_t>(Fr) | reinterpret_cast<uintptr_t>(Br)) & 7) == 0) {
+        float2 *F2 = reinterpret_cast<float2 *>(Fr);
+        float2 *B2 = reinterpret_cast<float2 *>(Br);
+        F2[0] = f2(v.F[0].x, v.F[1].x);
+        F2[1] = f2(v.F[2].x, v.F[0].y);
+        F2[2] = f2(v.F[1].y, v.F[2].y);
+        B2[0] = f2(v.B[0].x, v.B[1].x);
+        B2[1] = f2(v.B[2].x, v.B[0].y);
+        B2[2] = f2(v.B[1].y, v.B[2].y);
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         if (o0) {
@@ -181,16 +192,231 @@ struct Ctl {
     bool o0, o1;           // this lane writes p0 / p1
 };
 
-// One row step: load row r, finish the weights of row r-1, sweep 1 at row r-1 and
+// ------------------------------------------------------------------ row sources
+
+// Register variant: plain loads of row r+1 issued while row r is processed.
+template <typename T>
+struct RegSource {
+    Raw nxt;
+
+    __device__ __forceinline__ void load(const PassArgs &p, const LaneGeo &g, int r, Raw &o) {
+        const int gy = nearest_src(r, p.Ih, p.h);
+        const int sy = nearest_src(r, p.sh, p.h);
+        const T *Ir = static_cast<const T *>(p.I) + (long long)gy * p.I_pitch;
+        const T *Ar = static_cast<const T *>(p.A) + (long long)gy * p.A_pitch;
+        const T *Fr = static_cast<const T *>(p.Fs) + (long long)sy * p.s_pitch;
+        const T *Br = static_cast<const T *>(p.Bs) + (long long)sy * p.s_pitch;
+        o.a0 = ld_elem(Ar + g.gi0);
+        o.a1 = ld_elem(Ar + g.gi1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o.i0[c] = ld_elem(Ir + 3 * g.gi0 + c);
+            o.i1[c] = ld_elem(Ir + 3 * g.gi1 + c);
+            o.f0[c] = ld_elem(Fr + 3 * g.gs0 + c);
+            o.f1[c] = ld_elem(Fr + 3 * g.gs1 + c);
+            o.b0[c] = ld_elem(Br + 3 * g.gs0 + c);
+            o.b1[c] = ld_elem(Br + 3 * g.gs1 + c);
+        }
+    }
+    __device__ __forceinline__ bool start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
+        load(p, g, ct.r_first, nxt);
+        return true;
+    }
+    __device__ __forceinline__ bool get(const PassArgs &p, const LaneGeo &g, const Ctl &ct, int r,
+                                        Raw &out) {
+        out = nxt;
+        if (r + 1 <= ct.r_last) load(p, g, r + 1, nxt);
+        return true;
+    }
+    __device__ __forceinline__ void abort() {}
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+
+// floor((2r + 1) S / (2D)) for r = r0, r0 + 1, ... without a division per row.
+struct RowMap {
+    int q, rem, dq, drem, den;
+    __device__ __forceinline__ void init(int r0, int S, int D) {
+        const unsigned num = (2u * (unsigned)r0 + 1u) * (unsigned)S;
+        den = 2 * D;
+        q = (int)(num / (unsigned)den);
+        rem = (int)(num % (unsigned)den);
+        dq = (2 * S) / den;
+        drem = (2 * S) % den;
+    }
+    __device__ __forceinline__ int next() {
+        const int v = q;
+        q += dq;
+        rem += drem;
+        if (rem >= den) {
+            rem -= den;
+            ++q;
+        }
+        return v;
+    }
+};
+
+// Ring variant: the warp's rows r .. r + kRingSlots - 1 are in flight or resident in
+// shared memory; each slot holds the four source segments of a row (I, alpha, F, B)
+// at 16-byte aligned offsets, each segment copied as the 16-byte aligned superset of
+// its byte range by one bulk copy. A segment whose superset would leave its image
+// (possible only at the first or last image row) is copied by the lanes instead.
+template <typename T>
+struct RingSource {
+    unsigned char *slots;   // this warp's kRingSlots slots
+    uint32_t bar0;          // shared address of this warp's first mbarrier
+    int lane;
+    int giF, nI;            // first source column and column count of I / alpha
+    int gsF, nS;            // ... of the starting F / B
+    int li, la, ls;         // per-lane element offsets inside the segments
+    int dI, dS;             // column distance of the lane's second pixel from its first
+    uint32_t issued;        // bit s: slot s has a fill in flight
+    uint32_t parity;        // bit s: phase parity of slot s's fill in flight
+    RowMap fI, fS, gI, gS;  // source rows of the next row to fill / to take
+    const unsigned char *lo[4], *hi[4];   // byte extents of I, alpha, F, B
+
+    struct Seg {
+        const unsigned char *addr;
+        int len;
+    };
+
+    __device__ __forceinline__ void segs(const PassArgs &p, int gy, int sy, Seg *s) const {
+        const int es = (int)sizeof(T);
+        s[0].addr = static_cast<const unsigned char *>(p.I) + ((long long)gy * p.I_pitch + 3LL * giF) * es;
+        s[0].len = 3 * nI * es;
+        s[1].addr = static_cast<const unsigned char *>(p.A) + ((long long)gy * p.A_pitch + giF) * es;
+        s[1].len = nI * es;
+        s[2].addr = static_cast<const unsigned char *>(p.Fs) + ((long long)sy * p.s_pitch + 3LL * gsF) * es;
+        s[2].len = 3 * nS * es;
+        s[3].addr = static_cast<const unsigned char *>(p.Bs) + ((long long)sy * p.s_pitch + 3LL * gsF) * es;
+        s[3].len = 3 * nS * es;
+    }
+
+    __device__ __forceinline__ unsigned char *seg_dst(const PassArgs &p, int slot, int k) const {
+        unsigned char *b = slots + (size_t)slot * p.slot_bytes;
+        return b + (k == 0 ? 0 : k == 1 ? p.capI : k == 2 ? p.capI + p.capA : p.capI + p.capA + p.capS);
+    }
+
+    // Warp-collective: start filling `slot` with the next row; its fill has phase `par`.
+    __device__ __forceinline__ void fill(const PassArgs &p, int slot, uint32_t par) {
+        Seg s[4];
+        segs(p, fI.next(), fS.next(), s);
+        uint32_t tx = 0;
+        bool bulk[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(s[k].addr);
+            const uintptr_t a16 = a & ~(uintptr_t)15;
+            const uintptr_t e16 = (a + s[k].len + 15) & ~(uintptr_t)15;
+            bulk[k] = a16 >= reinterpret_cast<uintptr_t>(lo[k]) && e16 <= reinterpret_cast<uintptr_t>(hi[k]);
+            if (bulk[k]) {
+                tx += (uint32_t)(e16 - a16);
+            } else {
+                T *dst = reinterpret_cast<T *>(seg_dst(p, slot, k) + (a & 15));
+                const T *src = reinterpret_cast<const T *>(s[k].addr);
+                for (int e = lane; e < s[k].len / (int)sizeof(T); e += 32) dst[e] = src[e];
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const uint32_t bar = bar0 + 8u * (uint32_t)slot;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         :: "r"(bar), "r"(tx) : "memory");
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!bulk[k]) continue;
+                const uintptr_t a = reinterpret_cast<uintptr_t>(s[k].addr);
+                const uintptr_t a16 = a & ~(uintptr_t)15;
+                const uint32_t n = (uint32_t)(((a + s[k].len + 15) & ~(uintptr_t)15) - a16);
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                    :: "r"(smem_addr(seg_dst(p, slot, k))), "l"(a16), "r"(n), "r"(bar)
+                    : "memory");
+            }
+        }
+        issued |= 1u << slot;
+        parity = (parity & ~(1u << slot)) | (par << slot);
+    }
+
+    // Bounded wait for phase `par` of `slot`; warp-uniform result.
+    __device__ __forceinline__ bool wait(int slot, uint32_t par) const {
+        const uint32_t bar = bar0 + 8u * (uint32_t)slot;
+        uint32_t ok = 0;
+        for (long long i = 0; i < kWaitLimit && !ok; ++i) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(ok) : "r"(bar), "r"(par) : "memory");
+        }
+        return __all_sync(kFull, ok != 0);
+    }
+
+    __device__ __forceinline__ bool start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
+        fI.init(ct.r_first, p.Ih, p.h);
+        fS.init(ct.r_first, p.sh, p.h);
+        gI.init(ct.r_first, p.Ih, p.h);
+        gS.init(ct.r_first, p.sh, p.h);
+        for (int i = 0; i < kRingSlots && ct.r_first + i <= ct.r_last; ++i) fill(p, i, 0u);
+        return true;
+    }
+
+    __device__ __forceinline__ bool get(const PassArgs &p, const LaneGeo &g, const Ctl &ct, int r,
+                                        Raw &o) {
+        const int i = r - ct.r_first;
+        const int slot = i % kRingSlots;
+        const uint32_t par = (uint32_t)(i / kRingSlots) & 1u;
+        if (!wait(slot, par)) return false;
+        issued &= ~(1u << slot);
+        Seg s[4];
+        segs(p, gI.next(), gS.next(), s);
+        const T *I = reinterpret_cast<const T *>(seg_dst(p, slot, 0) + (reinterpret_cast<uintptr_t>(s[0].addr) & 15));
+        const T *A = reinterpret_cast<const T *>(seg_dst(p, slot, 1) + (reinterpret_cast<uintptr_t>(s[1].addr) & 15));
+        const T *F = reinterpret_cast<const T *>(seg_dst(p, slot, 2) + (reinterpret_cast<uintptr_t>(s[2].addr) & 15));
+        const T *B = reinterpret_cast<const T *>(seg_dst(p, slot, 3) + (reinterpret_cast<uintptr_t>(s[3].addr) & 15));
+        o.a0 = to_f(A[la]);
+        o.a1 = to_f(A[la + dI]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o.i0[c] = to_f(I[li + c]);
+            o.i1[c] = to_f(I[li + 3 * dI + c]);
+            o.f0[c] = to_f(F[ls + c]);
+            o.f1[c] = to_f(F[ls + 3 * dS + c]);
+            o.b0[c] = to_f(B[ls + c]);
+            o.b1[c] = to_f(B[ls + 3 * dS + c]);
+        }
+        __syncwarp();   // every lane has read the slot before it is refilled
+        if (r + kRingSlots <= ct.r_last) fill(p, slot, par ^ 1u);
+        return true;
+    }
+
+    // After a failed wait: wait (bounded) for every fill still in flight, then return.
+    __device__ __forceinline__ void abort() const {
+        for (int s = 0; s < kRingSlots; ++s)
+            if (issued & (1u << s)) wait(s, (parity >> s) & 1u);
+    }
+};
+
+// ------------------------------------------------------------------ the pass
+
+// One row step: take row r, finish the weights of row r-1, sweep 1 at row r-1 and
 // (K == 2) sweep 2 at row r-2. Queue arguments are the rows r, r-1, r-2 (S: row data,
-// Q: starting state) and r-1, r-2, r-3 (P: sweep-1 state).
-template <typename T, int K, bool CLAMP>
-__device__ __forceinline__ void step(const PassArgs &p, const LaneGeo &g, const Ctl &ct, int r,
-                                     Raw &nxt, RowK &Sr, RowK &Sr1, RowK &Sr2,
+// Q: starting state) and r-1, r-2, r-3 (P: sweep-1 state). Returns false if a bounded
+// wait gave up.
+template <typename T, int K, bool CLAMP, typename Src>
+__device__ __forceinline__ bool step(const PassArgs &p, const LaneGeo &g, const Ctl &ct, int r,
+                                     Src &src, RowK &Sr, RowK &Sr1, RowK &Sr2,
                                      FB &Qr, FB &Qr1, FB &Qr2, FB &Pw, FB &Pr2, FB &Pr3) {
     if (r <= ct.r_last) {
-        const Raw cur = nxt;
-        if (r + 1 <= ct.r_last) load_raw<T>(p, g, r + 1, nxt);
+        Raw cur;
+        if (!src.get(p, g, ct, r, cur)) return false;
         make_row(cur, g, r, Sr1, p.eps, p.omega, Sr, Qr);
     }
     const int q = r - 1;
@@ -201,6 +427,7 @@ __device__ __forceinline__ void step(const PassArgs &p, const LaneGeo &g, const 
             Sr1.wd = f2(0.f, 0.f);   // bottom row: the neighbour below is the pixel itself
             Sr1.ws = add2(Sr1.ws, f2(p.eps, p.eps));
         }
+        finish_row(Sr1);
     }
     if (K == 1) {
         if (q >= ct.Y0 && q < ct.Y1) {
@@ -217,6 +444,7 @@ __device__ __forceinline__ void step(const PassArgs &p, const LaneGeo &g, const 
             store_row<T>(p, g, q2, res, ct.o0, ct.o1);
         }
     }
+    return true;
 }
 
 __device__ __forceinline__ void zero(FB &v) {
@@ -224,36 +452,25 @@ __device__ __forceinline__ void zero(FB &v) {
     for (int c = 0; c < 3; ++c) v.F[c] = v.B[c] = f2(0.f, 0.f);
 }
 __device__ __forceinline__ void zero(RowK &v) {
-    v.a = v.wl = v.wr = v.wu = v.wd = v.ws = f2(0.f, 0.f);
+    v.a = v.wl = v.wr = v.wu = v.wd = v.ws = v.mFF = v.mBB = v.nFB = f2(0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < 3; ++c) v.I[c] = f2(0.f, 0.f);
 }
 
-template <typename T, int K, bool CLAMP>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_kernel(const PassArgs p) {
-    const int lane = threadIdx.x & 31;
-    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (warp >= p.n_warps) return;
+__device__ __forceinline__ void lane_setup(const PassArgs &p, int warp, int lane, LaneGeo &g,
+                                           Ctl &ct, int K) {
     const int xs = warp % p.n_xstrips;
     const int ys = warp / p.n_xstrips;
-
-    LaneGeo g;
     g.x = xs * kStripW - 2 + 2 * lane;
     const int xc0 = min(max(g.x, 0), p.w - 1);
     const int xc1 = min(max(g.x + 1, 0), p.w - 1);
-    const int gi0 = nearest_src(xc0, p.Iw, p.w), gi1 = nearest_src(xc1, p.Iw, p.w);
-    const int gs0 = nearest_src(xc0, p.sw, p.w), gs1 = nearest_src(xc1, p.sw, p.w);
-    g.oi0 = 3 * gi0;
-    g.oi1 = 3 * gi1;
-    g.oa0 = gi0;
-    g.oa1 = gi1;
-    g.os0 = 3 * gs0;
-    g.os1 = 3 * gs1;
+    g.gi0 = nearest_src(xc0, p.Iw, p.w);
+    g.gi1 = nearest_src(xc1, p.Iw, p.w);
+    g.gs0 = nearest_src(xc0, p.sw, p.w);
+    g.gs1 = nearest_src(xc1, p.sw, p.w);
     g.inL0 = g.x > 0;
     g.inR0 = g.x + 1 < p.w;
     g.inR1 = g.x + 2 < p.w;
-
-    Ctl ct;
     ct.Y0 = ys * p.strip_h;
     ct.Y1 = min(ct.Y0 + p.strip_h, p.h);
     ct.r_first = max(ct.Y0 - K, 0);
@@ -263,23 +480,96 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_kernel(cons
     const bool mid = lane >= 1 && lane <= 30;
     ct.o0 = mid && g.x < p.w;
     ct.o1 = mid && g.x + 1 < p.w;
+}
 
+template <typename T, int K, bool CLAMP, typename Src>
+__device__ __forceinline__ void run_strip(const PassArgs &p, const LaneGeo &g, const Ctl &ct,
+                                          Src &src) {
     RowK S0, S1, S2;
     FB Q0, Q1, Q2, P0, P1, P2;
     zero(S0); zero(S1); zero(S2);
     zero(Q0); zero(Q1); zero(Q2);
     zero(P0); zero(P1); zero(P2);
-    Raw nxt;
-    load_raw<T>(p, g, ct.r_first, nxt);
-
+    if (!src.start(p, g, ct)) return;
     const int r_end = ct.r_last + K;
-    for (int r = ct.r_first; r <= r_end; r += 3) {
-        step<T, K, CLAMP>(p, g, ct, r, nxt, S0, S2, S1, Q0, Q2, Q1, P2, P1, P0);
-        if (r + 1 > r_end) break;
-        step<T, K, CLAMP>(p, g, ct, r + 1, nxt, S1, S0, S2, Q1, Q0, Q2, P0, P2, P1);
-        if (r + 2 > r_end) break;
-        step<T, K, CLAMP>(p, g, ct, r + 2, nxt, S2, S1, S0, Q2, Q1, Q0, P1, P0, P2);
+    bool ok = true;
+    for (int r = ct.r_first; r <= r_end && ok; r += 3) {
+        ok = step<T, K, CLAMP>(p, g, ct, r, src, S0, S2, S1, Q0, Q2, Q1, P2, P1, P0);
+        if (!ok || r + 1 > r_end) break;
+        ok = step<T, K, CLAMP>(p, g, ct, r + 1, src, S1, S0, S2, Q1, Q0, Q2, P0, P2, P1);
+        if (!ok || r + 2 > r_end) break;
+        ok = step<T, K, CLAMP>(p, g, ct, r + 2, src, S2, S1, S0, Q2, Q1, Q0, P1, P0, P2);
     }
+    if (!ok) {
+        if ((threadIdx.x & 31) == 0) atomicExch(&g_device_error, 1);
+        src.abort();
+    }
+}
+
+template <typename T, int K, bool CLAMP>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_kernel(const PassArgs p) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (warp >= p.n_warps) return;
+    LaneGeo g;
+    Ctl ct;
+    lane_setup(p, warp, lane, g, ct, K);
+    RegSource<T> src;
+    run_strip<T, K, CLAMP>(p, g, ct, src);
+}
+
+template <typename T, int K, bool CLAMP>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_ring_kernel(const PassArgs p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (warp >= p.n_warps) return;
+    LaneGeo g;
+    Ctl ct;
+    lane_setup(p, warp, lane, g, ct, K);
+
+    RingSource<T> src;
+    src.lane = lane;
+    src.slots = smem + (size_t)wib * kRingSlots * p.slot_bytes;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(
+        smem + (size_t)kWarpsPerBlock * kRingSlots * p.slot_bytes) + wib * kRingSlots;
+    src.bar0 = smem_addr(bars);
+    src.issued = 0;
+    // the warp's source column ranges: lanes load columns [xf, xl] of the level
+    const int X0 = g.x - 2 * lane;
+    const int xf = min(max(X0, 0), p.w - 1);
+    const int xl = min(max(X0 + kLaneCols - 1, 0), p.w - 1);
+    src.giF = nearest_src(xf, p.Iw, p.w);
+    src.nI = nearest_src(xl, p.Iw, p.w) - src.giF + 1;
+    src.gsF = nearest_src(xf, p.sw, p.w);
+    src.nS = nearest_src(xl, p.sw, p.w) - src.gsF + 1;
+    src.li = 3 * (g.gi0 - src.giF);
+    src.la = g.gi0 - src.giF;
+    src.ls = 3 * (g.gs0 - src.gsF);
+    src.dI = g.gi1 - g.gi0;
+    src.dS = g.gs1 - g.gs0;
+    src.parity = 0;
+    const int es = (int)sizeof(T);
+    const unsigned char *Ib = static_cast<const unsigned char *>(p.I);
+    const unsigned char *Ab = static_cast<const unsigned char *>(p.A);
+    const unsigned char *Fb = static_cast<const unsigned char *>(p.Fs);
+    const unsigned char *Bb = static_cast<const unsigned char *>(p.Bs);
+    src.lo[0] = Ib;
+    src.hi[0] = Ib + ((long long)(p.Ih - 1) * p.I_pitch + 3LL * p.Iw) * es;
+    src.lo[1] = Ab;
+    src.hi[1] = Ab + ((long long)(p.Ih - 1) * p.A_pitch + p.Iw) * es;
+    src.lo[2] = Fb;
+    src.hi[2] = Fb + ((long long)(p.sh - 1) * p.s_pitch + 3LL * p.sw) * es;
+    src.lo[3] = Bb;
+    src.hi[3] = Bb + ((long long)(p.sh - 1) * p.s_pitch + 3LL * p.sw) * es;
+    if (lane == 0) {
+        for (int s = 0; s < kRingSlots; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(src.bar0 + 8u * s) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    run_strip<T, K, CLAMP>(p, g, ct, src);
 }
 
 // Zero sweeps: the level's F and B are the nearest resize of the starting state.
@@ -308,6 +598,17 @@ cudaError_t launch_t(const PassArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <typename T, int K, bool CLAMP>
+cudaError_t launch_ring_t(const PassArgs &a, cudaStream_t s) {
+    const int blocks = (a.n_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const size_t smem = level_pass_ring_smem(a.slot_bytes);
+    cudaError_t e = cudaFuncSetAttribute(level_pass_ring_kernel<T, K, CLAMP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    level_pass_ring_kernel<T, K, CLAMP><<<blocks, kWarpsPerBlock * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_dtype(int iters, int clamp, const PassArgs &a, cudaStream_t s) {
     if (iters == 0) {
@@ -318,6 +619,13 @@ cudaError_t launch_dtype(int iters, int clamp, const PassArgs &a, cudaStream_t s
     }
     if (iters == 1) return clamp ? launch_t<T, 1, true>(a, s) : launch_t<T, 1, false>(a, s);
     return clamp ? launch_t<T, 2, true>(a, s) : launch_t<T, 2, false>(a, s);
+}
+
+template <typename T>
+cudaError_t launch_ring_dtype(int iters, int clamp, const PassArgs &a, cudaStream_t s) {
+    if (iters == 1) return clamp ? launch_ring_t<T, 1, true>(a, s) : launch_ring_t<T, 1, false>(a, s);
+    if (iters == 2) return clamp ? launch_ring_t<T, 2, true>(a, s) : launch_ring_t<T, 2, false>(a, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -331,6 +639,51 @@ cudaError_t launch_level_pass(int dtype, int iters, int clamp, const PassArgs &a
         case kF16: return launch_dtype<__half>(iters, clamp, a, s);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_level_pass_ring(int dtype, int iters, int clamp, const PassArgs &a,
+                                   cudaStream_t s) {
+    if (a.slot_bytes <= 0 || (a.slot_bytes & 15) || (a.capI & 15) || (a.capA & 15) ||
+        (a.capS & 15))
+        return cudaErrorInvalidValue;
+    switch (dtype) {
+        case kF32: return launch_ring_dtype<float>(iters, clamp, a, s);
+        case kBF16: return launch_ring_dtype<__nv_bfloat16>(iters, clamp, a, s);
+        case kF16: return launch_ring_dtype<__half>(iters, clamp, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+size_t level_pass_ring_smem(int slot_bytes) {
+    return (size_t)kWarpsPerBlock * kRingSlots * (size_t)slot_bytes +
+           (size_t)kWarpsPerBlock * kRingSlots * 8;
+}
+
+int strip_span(int S, int D) {
+    int best = 1;
+    const int nx = (D + kStripW - 1) / kStripW;
+    for (int xs = 0; xs < nx; ++xs) {
+        const int X0 = xs * kStripW - 2;
+        const int xf = std::min(std::max(X0, 0), D - 1);
+        const int xl = std::min(std::max(X0 + kLaneCols - 1, 0), D - 1);
+        best = std::max(best, nearest_src(xl, S, D) - nearest_src(xf, S, D) + 1);
+    }
+    return best;
+}
+
+cudaError_t read_and_clear_device_error(int *code, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyFromSymbolAsync(code, g_device_error, sizeof(int), 0,
+                                              cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (*code) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbolAsync(g_device_error, &zero, sizeof(int), 0,
+                                    cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    return e;
 }
 
 int level_pass_strip_width() { return kStripW; }

@@ -1,0 +1,54 @@
+"""Runs one kernel case a few times, for profiler captures (ncu -k ... -s <warm-up> -c ...).
+
+    python -m paper_2006_14970_gb300.profile_case level_pass 4096 2304 [--repeat 4]
+    python -m paper_2006_14970_gb300.profile_case estimate 2048 1536 [--dtype bf16]
+
+level_pass: the top-level pass of a W x H image (sweeps of the top level, starting F/B
+gathered from the level below it), the dominant launch of a solve.
+estimate: complete fg_estimate calls.
+Inputs come from the seeded synthetic generator; nothing is checked here.
+"""
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+from . import build as _build
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["level_pass", "estimate"])
+    ap.add_argument("w", type=int)
+    ap.add_argument("h", type=int)
+    ap.add_argument("--repeat", type=int, default=4)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    a = ap.parse_args()
+    _build.build()
+    from . import fgml, synth
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
+    s = synth.make_sample(a.w, a.h, synth.SEED_BASE + 50)
+    I = torch.from_numpy(s.I).cuda().to(dt)
+    A = torch.from_numpy(s.alpha).cuda().to(dt)
+    if a.case == "level_pass":
+        levels = fgml.schedule(a.w, a.h)
+        (pw, ph, _), (_, _, k) = levels[-2], levels[-1]
+        g = torch.Generator(device="cuda").manual_seed(1)
+        Fs = torch.rand((ph, pw, 3), device="cuda", generator=g).to(dt)
+        Bs = torch.rand((ph, pw, 3), device="cuda", generator=g).to(dt)
+        F = torch.empty_like(I)
+        B = torch.empty_like(I)
+        for _ in range(a.repeat):
+            fgml.level_pass(I, A, Fs, Bs, k, a.w, a.h, None, F, B)
+    else:
+        F = torch.empty_like(I)
+        B = torch.empty_like(I)
+        for _ in range(a.repeat):
+            fgml.estimate(I, A, None, F, B)
+    torch.cuda.synchronize()
+    print(f"{a.case} {a.w}x{a.h} {a.dtype} x{a.repeat}: ok")
+
+
+if __name__ == "__main__":
+    main()

@@ -162,3 +162,24 @@ def test_full_size_8k_parity(fgml):
     F, B = _gpu_ml(fgml, s.I, s.alpha)
     Fo, Bo = oracle.ml(s.I, s.alpha)
     _assert_close(F, B, Fo, Bo, what="7680x4320")
+
+
+def test_unaligned_base_pointers(fgml):
+    # image rows and bases off the 16-byte grid: the row ring copies such segments by
+    # lanes instead of bulk copies, with the same results
+    for w, h, off in [(301, 97, 1), (1939, 64, 3), (64, 40, 2)]:
+        I, a = _random_inputs(w, h, 40 + off)
+        Ib = torch.empty(h * w * 3 + off, device="cuda")
+        Ab = torch.empty(h * w + off, device="cuda")
+        Iv = Ib[off:].view(h, w, 3)
+        Av = Ab[off:].view(h, w)
+        Iv.copy_(_dev(I))
+        Av.copy_(_dev(a))
+        Fb = torch.empty(h * w * 3 + off, device="cuda")
+        Bb = torch.empty(h * w * 3 + off, device="cuda")
+        F, B = fgml.estimate(Iv, Av, None, Fb[off:].view(h, w, 3), Bb[off:].view(h, w, 3))
+        torch.cuda.synchronize()
+        Fo, Bo = oracle.ml(I, a)
+        _assert_close(F.cpu().numpy().astype(np.float64), B.cpu().numpy().astype(np.float64),
+                      Fo, Bo, what=f"unaligned {w}x{h}+{off}")
+    fgml.sync()   # no bounded wait gave up
