@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <utility>
 #include <vector>
@@ -198,17 +199,23 @@ struct State {
     int w, h;
 };
 
+// Rows of a workspace state are padded to 16 bytes so that tensor copies can read them.
+long long state_pitch(int w, int es) {
+    const long long q = 16 / es;
+    return (3LL * w + q - 1) / q * q;
+}
+
 size_t state_bytes(int w, int h, int es) {
-    const size_t plane = ((size_t)w * h * 3 * es + 255) & ~(size_t)255;
+    const size_t plane = ((size_t)state_pitch(w, es) * h * es + 255) & ~(size_t)255;
     return 2 * plane;
 }
 
 State state_in(const Buf &b, int w, int h, int es) {
-    const size_t plane = ((size_t)w * h * 3 * es + 255) & ~(size_t)255;
+    const size_t plane = ((size_t)state_pitch(w, es) * h * es + 255) & ~(size_t)255;
     State s;
     s.F = b.p;
     s.B = (const char *)b.p + plane;
-    s.pitch = 3LL * w;
+    s.pitch = state_pitch(w, es);
     s.w = w;
     s.h = h;
     return s;
@@ -222,9 +229,6 @@ struct Input {
     int w, h;
 };
 
-// Shared memory of one ring-variant block; two blocks must fit on an SM.
-constexpr size_t kRingSmemBudget = 110 * 1024;
-
 // Rows per warp of a level pass: enough warps for several waves of resident warps.
 int strip_rows(int w, int h) {
     const int nx = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
@@ -233,6 +237,79 @@ int strip_rows(int w, int h) {
     r = std::max<long long>(r, 4);
     r = std::min<long long>(r, 512);
     return (int)r;
+}
+
+// Shared memory of one ring- or tile-variant block; two blocks must fit on an SM.
+constexpr size_t kRingSmemBudget = 110 * 1024;
+
+// ------------------------------------------------------------------ tensor maps
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// A 2D tensor map of `rows` rows of `inner` elements, `pitch` bytes apart; false if the
+// layout does not allow tensor copies (base or pitch off the 16-byte grid).
+bool make_map(CUtensorMap *m, int dtype, const void *base, long long inner, long long rows,
+              long long pitch, int box_x, int box_y) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (pitch & 15) || box_x > 256 ||
+        box_y > 256 || box_x < 1 || box_y < 1)
+        return false;
+    const CUtensorMapDataType dt = dtype == kF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dtype == kBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Fills the tile-variant fields of `a` and builds its maps; false if not applicable.
+bool plan_tile(int dtype, const Input &in, const State &src, PassArgs &a, TileMaps &m) {
+    if (in.w != a.w || in.h != a.h) return false;   // I and alpha must be the input itself
+    const int es = dtype == kF32 ? 4 : 2;
+    const int q = 16 / es, R = level_pass_tile_rows();
+    auto up = [](int v, int k) { return (v + k - 1) / k * k; };
+    auto r128 = [](int v) { return (v + 127) & ~127; };
+    a.tile_bwI = up(3 * 64 + q - 1, q);
+    a.tile_bwA = up(64 + q - 1, q);
+    a.tile_bwS = up(3 * strip_span(src.w, a.w) + q - 1, q);
+    int rs = 1;
+    for (int r0 = 0; r0 < a.h; ++r0) {
+        const int r1 = std::min(r0 + R - 1, a.h - 1);
+        rs = std::max(rs, nearest_src(r1, src.h, a.h) - nearest_src(r0, src.h, a.h) + 1);
+    }
+    a.tile_rs = rs;
+    a.tile_offA = r128(R * a.tile_bwI * es);
+    a.tile_offF = a.tile_offA + r128(R * a.tile_bwA * es);
+    a.tile_offB = a.tile_offF + r128(rs * a.tile_bwS * es);
+    a.tile_chunk = a.tile_offB + r128(rs * a.tile_bwS * es);
+    a.tile_tx = R * (a.tile_bwI + a.tile_bwA) * es + 2 * rs * a.tile_bwS * es;
+    if (level_pass_tile_smem(a.tile_chunk) > kRingSmemBudget) return false;
+    return make_map(&m.I, dtype, in.I, 3LL * in.w, in.h, in.I_pitch * es, a.tile_bwI, R) &&
+           make_map(&m.A, dtype, in.A, in.w, in.h, in.A_pitch * es, a.tile_bwA, R) &&
+           make_map(&m.F, dtype, src.F, 3LL * src.w, src.h, src.pitch * es, a.tile_bwS, rs) &&
+           make_map(&m.B, dtype, src.B, 3LL * src.w, src.h, src.pitch * es, a.tile_bwS, rs);
 }
 
 cudaError_t pass(int dtype, int iters, int clamp, const fg_params &p, const Input &in,
@@ -262,6 +339,8 @@ cudaError_t pass(int dtype, int iters, int clamp, const fg_params &p, const Inpu
     a.n_warps = a.n_xstrips * ((h + a.strip_h - 1) / a.strip_h);
     a.capI = a.capA = a.capS = a.slot_bytes = 0;
     if (iters == 1 || iters == 2) {
+        TileMaps maps;
+        if (plan_tile(dtype, in, src, a, maps)) return launch_level_pass_tile(dtype, iters, clamp, a, maps, s);
         // ring slots: each segment's 16-byte aligned superset (up to 30 extra bytes)
         const int es = dtype == kF32 ? 4 : 2;
         auto r16 = [](int v) { return (v + 15) & ~15; };
@@ -270,6 +349,10 @@ cudaError_t pass(int dtype, int iters, int clamp, const fg_params &p, const Inpu
         a.capA = r16(spanI * es + 30);
         a.capS = r16(3 * spanS * es + 30);
         a.slot_bytes = a.capI + a.capA + 2 * a.capS;
+        a.I_end = (const char *)in.I + ((long long)(in.h - 1) * in.I_pitch + 3LL * in.w) * es;
+        a.A_end = (const char *)in.A + ((long long)(in.h - 1) * in.A_pitch + in.w) * es;
+        a.Fs_end = (const char *)src.F + ((long long)(src.h - 1) * src.pitch + 3LL * src.w) * es;
+        a.Bs_end = (const char *)src.B + ((long long)(src.h - 1) * src.pitch + 3LL * src.w) * es;
         if (level_pass_ring_smem(a.slot_bytes) <= kRingSmemBudget)
             return launch_level_pass_ring(dtype, iters, clamp, a, s);
     }

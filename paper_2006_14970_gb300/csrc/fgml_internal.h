@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libfgml.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -54,6 +55,17 @@ struct PassArgs {
     int n_warps;            // n_xstrips * ceil(h / strip_h)
     // row-ring variant only: bytes of each segment of a ring slot (multiples of 16)
     int capI, capA, capS, slot_bytes;
+    // row-ring variant only: one past the last byte of I, alpha, Fs and Bs
+    const void *I_end, *A_end, *Fs_end, *Bs_end;
+    // tile variant only: box widths (elements), source rows per chunk, chunk layout (bytes)
+    int tile_bwI, tile_bwA, tile_bwS, tile_rs;
+    int tile_offA, tile_offF, tile_offB, tile_chunk, tile_tx;
+};
+
+// Tensor maps of the tile variant: I, alpha, and the starting F and B, as 2D tensors of
+// elements (row length = channels x width).
+struct TileMaps {
+    CUtensorMap I, A, F, B;
 };
 
 // Largest source-column span (in pixels) of one warp strip of a level pass, for a gather
@@ -91,6 +103,12 @@ cudaError_t launch_level_pass(int dtype, int iters, int clamp, const PassArgs &a
 cudaError_t launch_level_pass_ring(int dtype, int iters, int clamp, const PassArgs &a,
                                    cudaStream_t s);
 size_t level_pass_ring_smem(int slot_bytes);
+// Tile variant (2D tensor copies of multi-row boxes): for levels whose I and alpha are the
+// full-resolution input; a.tile_* must be filled in and the maps built for them.
+cudaError_t launch_level_pass_tile(int dtype, int iters, int clamp, const PassArgs &a,
+                                   const TileMaps &m, cudaStream_t s);
+size_t level_pass_tile_smem(int chunk_bytes);
+int level_pass_tile_rows();
 // Device error word of the library's bounded waits (0 = no error).
 cudaError_t read_and_clear_device_error(int *code, cudaStream_t s);
 cudaError_t launch_coarse(int dtype, int clamp, const CoarseArgs &a, cudaStream_t s);

@@ -39,7 +39,14 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kStripW = 60;          // output columns per warp
 constexpr int kWarpsPerBlock = 4;
 constexpr int kLaneCols = 64;        // columns held by a warp (2 per lane)
-constexpr long long kWaitLimit = 1LL << 22;   // try_wait polls before a wait gives up
+constexpr int kWaitPolls = 1 << 20;          // try_wait polls before a wait gives up
+constexpr uint32_t kWaitHintNs = 2000;       // suspend-time hint of one poll
+constexpr int kTileRows = 4;                 // rows per tensor-copy chunk
+constexpr int kTileSlots = 3;                // chunks in flight per warp
+#ifndef FGML_RING_MIN_BLOCKS
+#define FGML_RING_MIN_BLOCKS 2
+#endif
+constexpr int kRingMinBlocks = FGML_RING_MIN_BLOCKS;   // resident blocks per SM targeted
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -156,12 +163,19 @@ __device__ __forceinline__ void update(const RowK &k, const FB &c, const FB &up,
     }
 }
 
+// Output pointers of a lane: the bytes of its first pixel in row 0 of F and B.
+struct Out {
+    unsigned char *F, *B;
+    long long pitch;        // bytes
+    bool o0, o1;            // this lane writes p0 / p1
+};
+
 template <typename T>
-__device__ __forceinline__ void store_row(const PassArgs &p, const LaneGeo &g, int r,
-                                          const FB &v, bool o0, bool o1) {
-    T *Fr = static_cast<T *>(p.Fd) + (long long)r * p.d_pitch + 3 * g.x;
-    T *Br = static_cast<T *>(p.Bd) + (long long)r * p.d_pitch + 3 * g.x;
-    if (sizeof(T) == 4 && o0 && o1 && ((reinterpret_cast<uintptr_t>(Fr) | reinterpret_cast<uintptr_t>(Br)) & 7) == 0) {
+__device__ __forceinline__ void store_row(const Out &o, int r, const FB &v) {
+    T *Fr = reinterpret_cast<T *>(o.F + (long long)r * o.pitch);
+    T *Br = reinterpret_cast<T *>(o.B + (long long)r * o.pitch);
+    if (sizeof(T) == 4 && o.o0 && o.o1 &&
+        (((uint32_t)reinterpret_cast<uintptr_t>(Fr) | (uint32_t)reinterpret_cast<uintptr_t>(Br)) & 7) == 0) {
         float2 *F2 = reinterpret_cast<float2 *>(Fr);
         float2 *B2 = reinterpret_cast<float2 *>(Br);
         F2[0] = f2(v.F[0].x, v.F[1].x);
@@ -174,11 +188,11 @@ __device__ __forceinline__ void store_row(const PassArgs &p, const LaneGeo &g, i
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        if (o0) {
+        if (o.o0) {
             st_elem(Fr + c, v.F[c].x);
             st_elem(Br + c, v.B[c].x);
         }
-        if (o1) {
+        if (o.o1) {
             st_elem(Fr + 3 + c, v.F[c].y);
             st_elem(Br + 3 + c, v.B[c].y);
         }
@@ -189,7 +203,6 @@ struct Ctl {
     int r_first, r_last;   // rows loaded
     int t1_lo, t1_hi;      // rows of sweep 1 (for K == 2)
     int Y0, Y1;            // output rows [Y0, Y1)
-    bool o0, o1;           // this lane writes p0 / p1
 };
 
 // ------------------------------------------------------------------ row sources
@@ -218,9 +231,8 @@ struct RegSource {
             o.b1[c] = ld_elem(Br + 3 * g.gs1 + c);
         }
     }
-    __device__ __forceinline__ bool start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
+    __device__ __forceinline__ void start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
         load(p, g, ct.r_first, nxt);
-        return true;
     }
     __device__ __forceinline__ bool get(const PassArgs &p, const LaneGeo &g, const Ctl &ct, int r,
                                         Raw &out) {
@@ -263,138 +275,179 @@ struct RowMap {
 };
 
 // Ring variant: the warp's rows r .. r + kRingSlots - 1 are in flight or resident in
-// shared memory; each slot holds the four source segments of a row (I, alpha, F, B)
-// at 16-byte aligned offsets, each segment copied as the 16-byte aligned superset of
-// its byte range by one bulk copy. A segment whose superset would leave its image
-// (possible only at the first or last image row) is copied by the lanes instead.
+// shared memory. A slot holds the four source segments of a row (I, alpha, F, B), each
+// at a 16-byte aligned offset and copied by one bulk copy as the 16-byte aligned
+// superset of its byte range. A segment whose superset could leave its image (only
+// possible in the first or last row of that image) is checked, and copied by the
+// lanes instead when it would.
 template <typename T>
 struct RingSource {
-    unsigned char *slots;   // this warp's kRingSlots slots
+    uint32_t slots_s;       // shared address of this warp's first slot
     uint32_t bar0;          // shared address of this warp's first mbarrier
     int lane;
-    int giF, nI;            // first source column and column count of I / alpha
-    int gsF, nS;            // ... of the starting F / B
-    int li, la, ls;         // per-lane element offsets inside the segments
-    int dI, dS;             // column distance of the lane's second pixel from its first
+    int colI, colA, colS;   // byte offset of the strip's first source column in a row
+    int lenI, lenA, lenS;   // bytes of each segment
+    int li, la, ls, dI, dS; // per-lane element offsets inside the segments
+    int fslot, gslot;       // next slot to fill / to take
+    uint32_t fpar, gpar;    // their phase parities
     uint32_t issued;        // bit s: slot s has a fill in flight
     uint32_t parity;        // bit s: phase parity of slot s's fill in flight
     RowMap fI, fS, gI, gS;  // source rows of the next row to fill / to take
-    const unsigned char *lo[4], *hi[4];   // byte extents of I, alpha, F, B
 
-    struct Seg {
-        const unsigned char *addr;
-        int len;
-    };
-
-    __device__ __forceinline__ void segs(const PassArgs &p, int gy, int sy, Seg *s) const {
+    __device__ __forceinline__ const unsigned char *row_addr(const PassArgs &p, int k, int y) const {
         const int es = (int)sizeof(T);
-        s[0].addr = static_cast<const unsigned char *>(p.I) + ((long long)gy * p.I_pitch + 3LL * giF) * es;
-        s[0].len = 3 * nI * es;
-        s[1].addr = static_cast<const unsigned char *>(p.A) + ((long long)gy * p.A_pitch + giF) * es;
-        s[1].len = nI * es;
-        s[2].addr = static_cast<const unsigned char *>(p.Fs) + ((long long)sy * p.s_pitch + 3LL * gsF) * es;
-        s[2].len = 3 * nS * es;
-        s[3].addr = static_cast<const unsigned char *>(p.Bs) + ((long long)sy * p.s_pitch + 3LL * gsF) * es;
-        s[3].len = 3 * nS * es;
+        switch (k) {
+            case 0: return static_cast<const unsigned char *>(p.I) + (long long)y * p.I_pitch * es + colI;
+            case 1: return static_cast<const unsigned char *>(p.A) + (long long)y * p.A_pitch * es + colA;
+            case 2: return static_cast<const unsigned char *>(p.Fs) + (long long)y * p.s_pitch * es + colS;
+            default: return static_cast<const unsigned char *>(p.Bs) + (long long)y * p.s_pitch * es + colS;
+        }
+    }
+    __device__ __forceinline__ int seg_len(int k) const {
+        return k == 0 ? lenI : k == 1 ? lenA : lenS;
+    }
+    __device__ __forceinline__ uint32_t seg_off(const PassArgs &p, int k) const {
+        return k == 0 ? 0u : k == 1 ? (uint32_t)p.capI
+                                    : k == 2 ? (uint32_t)(p.capI + p.capA)
+                                             : (uint32_t)(p.capI + p.capA + p.capS);
     }
 
-    __device__ __forceinline__ unsigned char *seg_dst(const PassArgs &p, int slot, int k) const {
-        unsigned char *b = slots + (size_t)slot * p.slot_bytes;
-        return b + (k == 0 ? 0 : k == 1 ? p.capI : k == 2 ? p.capI + p.capA : p.capI + p.capA + p.capS);
-    }
-
-    // Warp-collective: start filling `slot` with the next row; its fill has phase `par`.
-    __device__ __forceinline__ void fill(const PassArgs &p, int slot, uint32_t par) {
-        Seg s[4];
-        segs(p, fI.next(), fS.next(), s);
+    // Warp-collective: start filling slot fslot with the next row.
+    __device__ __forceinline__ void fill(const PassArgs &p) {
+        const int gy = fI.next(), sy = fS.next();
+        const uint32_t slot_s = slots_s + (uint32_t)fslot * (uint32_t)p.slot_bytes;
+        const uint32_t bar = bar0 + 8u * (uint32_t)fslot;
+        const bool edgeI = gy == 0 || gy == p.Ih - 1;
+        const bool edgeS = sy == 0 || sy == p.sh - 1;
         uint32_t tx = 0;
         bool bulk[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const uintptr_t a = reinterpret_cast<uintptr_t>(s[k].addr);
-            const uintptr_t a16 = a & ~(uintptr_t)15;
-            const uintptr_t e16 = (a + s[k].len + 15) & ~(uintptr_t)15;
-            bulk[k] = a16 >= reinterpret_cast<uintptr_t>(lo[k]) && e16 <= reinterpret_cast<uintptr_t>(hi[k]);
+            const unsigned char *a = row_addr(p, k, k < 2 ? gy : sy);
+            const uintptr_t a16 = reinterpret_cast<uintptr_t>(a) & ~(uintptr_t)15;
+            const uint32_t n = ((((uint32_t)reinterpret_cast<uintptr_t>(a) & 15u) + (uint32_t)seg_len(k) + 15u) & ~15u);
+            bulk[k] = true;
+            if (k < 2 ? edgeI : edgeS) {
+                const void *lo = k == 0 ? p.I : k == 1 ? p.A : k == 2 ? p.Fs : p.Bs;
+                const void *hi = k == 0 ? p.I_end : k == 1 ? p.A_end : k == 2 ? p.Fs_end : p.Bs_end;
+                bulk[k] = a16 >= reinterpret_cast<uintptr_t>(lo) &&
+                          a16 + n <= reinterpret_cast<uintptr_t>(hi);
+            }
             if (bulk[k]) {
-                tx += (uint32_t)(e16 - a16);
+                tx += n;
             } else {
-                T *dst = reinterpret_cast<T *>(seg_dst(p, slot, k) + (a & 15));
-                const T *src = reinterpret_cast<const T *>(s[k].addr);
-                for (int e = lane; e < s[k].len / (int)sizeof(T); e += 32) dst[e] = src[e];
+                // the aligned superset would leave the image: copy the elements by lanes
+                const uint32_t dst = slot_s + seg_off(p, k) + ((uint32_t)reinterpret_cast<uintptr_t>(a) & 15u);
+                const T *src = reinterpret_cast<const T *>(a);
+                for (int e = lane; e < seg_len(k) / (int)sizeof(T); e += 32) {
+                    T v = src[e];
+                    unsigned short u;
+                    if (sizeof(T) == 4) {
+                        asm volatile("st.shared.b32 [%0], %1;" :: "r"(dst + 4u * e), "r"(__float_as_uint(*reinterpret_cast<float *>(&v))) : "memory");
+                    } else {
+                        u = *reinterpret_cast<unsigned short *>(&v);
+                        asm volatile("st.shared.b16 [%0], %1;" :: "r"(dst + 2u * e), "h"(u) : "memory");
+                    }
+                }
             }
         }
         __syncwarp();
         if (lane == 0) {
-            const uint32_t bar = bar0 + 8u * (uint32_t)slot;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                          :: "r"(bar), "r"(tx) : "memory");
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (!bulk[k]) continue;
-                const uintptr_t a = reinterpret_cast<uintptr_t>(s[k].addr);
-                const uintptr_t a16 = a & ~(uintptr_t)15;
-                const uint32_t n = (uint32_t)(((a + s[k].len + 15) & ~(uintptr_t)15) - a16);
+                const unsigned char *a = row_addr(p, k, k < 2 ? gy : sy);
+                const uintptr_t a16 = reinterpret_cast<uintptr_t>(a) & ~(uintptr_t)15;
+                const uint32_t n = ((((uint32_t)reinterpret_cast<uintptr_t>(a) & 15u) + (uint32_t)seg_len(k) + 15u) & ~15u);
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                    :: "r"(smem_addr(seg_dst(p, slot, k))), "l"(a16), "r"(n), "r"(bar)
+                    :: "r"(slot_s + seg_off(p, k)), "l"(a16), "r"(n), "r"(bar)
                     : "memory");
             }
         }
-        issued |= 1u << slot;
-        parity = (parity & ~(1u << slot)) | (par << slot);
+        issued |= 1u << fslot;
+        parity = (parity & ~(1u << fslot)) | (fpar << fslot);
+        if (++fslot == kRingSlots) {
+            fslot = 0;
+            fpar ^= 1u;
+        }
     }
 
     // Bounded wait for phase `par` of `slot`; warp-uniform result.
     __device__ __forceinline__ bool wait(int slot, uint32_t par) const {
         const uint32_t bar = bar0 + 8u * (uint32_t)slot;
         uint32_t ok = 0;
-        for (long long i = 0; i < kWaitLimit && !ok; ++i) {
+        for (int i = 0; i < kWaitPolls && !ok; ++i) {
             asm volatile(
                 "{\n\t.reg .pred p;\n\t"
-                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                 "selp.u32 %0, 1, 0, p;\n\t}"
-                : "=r"(ok) : "r"(bar), "r"(par) : "memory");
+                : "=r"(ok) : "r"(bar), "r"(par), "r"(kWaitHintNs) : "memory");
         }
         return __all_sync(kFull, ok != 0);
     }
 
-    __device__ __forceinline__ bool start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
+    __device__ __forceinline__ void start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
         fI.init(ct.r_first, p.Ih, p.h);
         fS.init(ct.r_first, p.sh, p.h);
         gI.init(ct.r_first, p.Ih, p.h);
         gS.init(ct.r_first, p.sh, p.h);
-        for (int i = 0; i < kRingSlots && ct.r_first + i <= ct.r_last; ++i) fill(p, i, 0u);
-        return true;
+        for (int i = 0; i < kRingSlots && ct.r_first + i <= ct.r_last; ++i) fill(p);
     }
 
     __device__ __forceinline__ bool get(const PassArgs &p, const LaneGeo &g, const Ctl &ct, int r,
                                         Raw &o) {
-        const int i = r - ct.r_first;
-        const int slot = i % kRingSlots;
-        const uint32_t par = (uint32_t)(i / kRingSlots) & 1u;
-        if (!wait(slot, par)) return false;
+        const int slot = gslot;
+        if (!wait(slot, gpar)) return false;
         issued &= ~(1u << slot);
-        Seg s[4];
-        segs(p, gI.next(), gS.next(), s);
-        const T *I = reinterpret_cast<const T *>(seg_dst(p, slot, 0) + (reinterpret_cast<uintptr_t>(s[0].addr) & 15));
-        const T *A = reinterpret_cast<const T *>(seg_dst(p, slot, 1) + (reinterpret_cast<uintptr_t>(s[1].addr) & 15));
-        const T *F = reinterpret_cast<const T *>(seg_dst(p, slot, 2) + (reinterpret_cast<uintptr_t>(s[2].addr) & 15));
-        const T *B = reinterpret_cast<const T *>(seg_dst(p, slot, 3) + (reinterpret_cast<uintptr_t>(s[3].addr) & 15));
-        o.a0 = to_f(A[la]);
-        o.a1 = to_f(A[la + dI]);
+        if (++gslot == kRingSlots) {
+            gslot = 0;
+            gpar ^= 1u;
+        }
+        const int gy = gI.next(), sy = gS.next();
+        const uint32_t slot_s = slots_s + (uint32_t)slot * (uint32_t)p.slot_bytes;
+        // slack of each segment inside its 16-byte aligned superset
+        const uint32_t sI = (uint32_t)reinterpret_cast<uintptr_t>(row_addr(p, 0, gy)) & 15u;
+        const uint32_t sA = (uint32_t)reinterpret_cast<uintptr_t>(row_addr(p, 1, gy)) & 15u;
+        const uint32_t sF = (uint32_t)reinterpret_cast<uintptr_t>(row_addr(p, 2, sy)) & 15u;
+        const uint32_t sB = (uint32_t)reinterpret_cast<uintptr_t>(row_addr(p, 3, sy)) & 15u;
+        const int es = (int)sizeof(T);
+        const uint32_t I = slot_s + sI + (uint32_t)(li * es);
+        const uint32_t A = slot_s + (uint32_t)p.capI + sA + (uint32_t)(la * es);
+        const uint32_t F = slot_s + (uint32_t)(p.capI + p.capA) + sF + (uint32_t)(ls * es);
+        const uint32_t B = slot_s + (uint32_t)(p.capI + p.capA + p.capS) + sB + (uint32_t)(ls * es);
+        o.a0 = lds<T>(A);
+        o.a1 = lds<T>(A + dI * es);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            o.i0[c] = to_f(I[li + c]);
-            o.i1[c] = to_f(I[li + 3 * dI + c]);
-            o.f0[c] = to_f(F[ls + c]);
-            o.f1[c] = to_f(F[ls + 3 * dS + c]);
-            o.b0[c] = to_f(B[ls + c]);
-            o.b1[c] = to_f(B[ls + 3 * dS + c]);
+            o.i0[c] = lds<T>(I + c * es);
+            o.i1[c] = lds<T>(I + (3 * dI + c) * es);
+            o.f0[c] = lds<T>(F + c * es);
+            o.f1[c] = lds<T>(F + (3 * dS + c) * es);
+            o.b0[c] = lds<T>(B + c * es);
+            o.b1[c] = lds<T>(B + (3 * dS + c) * es);
         }
         __syncwarp();   // every lane has read the slot before it is refilled
-        if (r + kRingSlots <= ct.r_last) fill(p, slot, par ^ 1u);
+        if (r + kRingSlots <= ct.r_last) fill(p);
         return true;
+    }
+
+    template <typename U>
+    __device__ __forceinline__ static float lds(uint32_t a) {
+        if (sizeof(U) == 4) {
+            float v;
+            asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+            return v;
+        } else {
+            unsigned short u;
+            asm volatile("ld.shared.b16 %0, [%1];" : "=h"(u) : "r"(a) : "memory");
+            U v;
+            *reinterpret_cast<unsigned short *>(&v) = u;
+            return to_f(v);
+        }
     }
 
     // After a failed wait: wait (bounded) for every fill still in flight, then return.
@@ -411,9 +464,10 @@ struct RingSource {
 // Q: starting state) and r-1, r-2, r-3 (P: sweep-1 state). Returns false if a bounded
 // wait gave up.
 template <typename T, int K, bool CLAMP, typename Src>
-__device__ __forceinline__ bool step(const PassArgs &p, const LaneGeo &g, const Ctl &ct, int r,
-                                     Src &src, RowK &Sr, RowK &Sr1, RowK &Sr2,
-                                     FB &Qr, FB &Qr1, FB &Qr2, FB &Pw, FB &Pr2, FB &Pr3) {
+__device__ __forceinline__ bool step(const PassArgs &p, const LaneGeo &g, const Ctl &ct,
+                                     const Out &out, int r, Src &src, RowK &Sr, RowK &Sr1,
+                                     RowK &Sr2, FB &Qr, FB &Qr1, FB &Qr2, FB &Pw, FB &Pr2,
+                                     FB &Pr3) {
     if (r <= ct.r_last) {
         Raw cur;
         if (!src.get(p, g, ct, r, cur)) return false;
@@ -433,7 +487,7 @@ __device__ __forceinline__ bool step(const PassArgs &p, const LaneGeo &g, const 
         if (q >= ct.Y0 && q < ct.Y1) {
             FB res;
             update<CLAMP>(Sr1, Qr1, Qr2, Qr, res);
-            store_row<T>(p, g, q, res, ct.o0, ct.o1);
+            store_row<T>(out, q, res);
         }
     } else {
         if (q >= ct.t1_lo && q <= ct.t1_hi) update<CLAMP>(Sr1, Qr1, Qr2, Qr, Pw);
@@ -441,7 +495,7 @@ __device__ __forceinline__ bool step(const PassArgs &p, const LaneGeo &g, const 
         if (q2 >= ct.Y0 && q2 < ct.Y1) {
             FB res;
             update<CLAMP>(Sr2, Pr2, Pr3, Pw, res);
-            store_row<T>(p, g, q2, res, ct.o0, ct.o1);
+            store_row<T>(out, q2, res);
         }
     }
     return true;
@@ -457,8 +511,9 @@ __device__ __forceinline__ void zero(RowK &v) {
     for (int c = 0; c < 3; ++c) v.I[c] = f2(0.f, 0.f);
 }
 
+template <typename T>
 __device__ __forceinline__ void lane_setup(const PassArgs &p, int warp, int lane, LaneGeo &g,
-                                           Ctl &ct, int K) {
+                                           Ctl &ct, Out &out, int K) {
     const int xs = warp % p.n_xstrips;
     const int ys = warp / p.n_xstrips;
     g.x = xs * kStripW - 2 + 2 * lane;
@@ -478,27 +533,31 @@ __device__ __forceinline__ void lane_setup(const PassArgs &p, int warp, int lane
     ct.t1_lo = max(ct.Y0 - 1, 0);
     ct.t1_hi = min(ct.Y1, p.h - 1);
     const bool mid = lane >= 1 && lane <= 30;
-    ct.o0 = mid && g.x < p.w;
-    ct.o1 = mid && g.x + 1 < p.w;
+    out.o0 = mid && g.x < p.w;
+    out.o1 = mid && g.x + 1 < p.w;
+    const long long col = 3LL * max(g.x, 0) * (long long)sizeof(T);
+    out.F = static_cast<unsigned char *>(p.Fd) + col;
+    out.B = static_cast<unsigned char *>(p.Bd) + col;
+    out.pitch = p.d_pitch * (long long)sizeof(T);
 }
 
 template <typename T, int K, bool CLAMP, typename Src>
 __device__ __forceinline__ void run_strip(const PassArgs &p, const LaneGeo &g, const Ctl &ct,
-                                          Src &src) {
+                                          const Out &out, Src &src) {
     RowK S0, S1, S2;
     FB Q0, Q1, Q2, P0, P1, P2;
     zero(S0); zero(S1); zero(S2);
     zero(Q0); zero(Q1); zero(Q2);
     zero(P0); zero(P1); zero(P2);
-    if (!src.start(p, g, ct)) return;
+    src.start(p, g, ct);
     const int r_end = ct.r_last + K;
     bool ok = true;
     for (int r = ct.r_first; r <= r_end && ok; r += 3) {
-        ok = step<T, K, CLAMP>(p, g, ct, r, src, S0, S2, S1, Q0, Q2, Q1, P2, P1, P0);
+        ok = step<T, K, CLAMP>(p, g, ct, out, r, src, S0, S2, S1, Q0, Q2, Q1, P2, P1, P0);
         if (!ok || r + 1 > r_end) break;
-        ok = step<T, K, CLAMP>(p, g, ct, r + 1, src, S1, S0, S2, Q1, Q0, Q2, P0, P2, P1);
+        ok = step<T, K, CLAMP>(p, g, ct, out, r + 1, src, S1, S0, S2, Q1, Q0, Q2, P0, P2, P1);
         if (!ok || r + 2 > r_end) break;
-        ok = step<T, K, CLAMP>(p, g, ct, r + 2, src, S2, S1, S0, Q2, Q1, Q0, P1, P0, P2);
+        ok = step<T, K, CLAMP>(p, g, ct, out, r + 2, src, S2, S1, S0, Q2, Q1, Q0, P1, P0, P2);
     }
     if (!ok) {
         if ((threadIdx.x & 31) == 0) atomicExch(&g_device_error, 1);
@@ -513,13 +572,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_kernel(cons
     if (warp >= p.n_warps) return;
     LaneGeo g;
     Ctl ct;
-    lane_setup(p, warp, lane, g, ct, K);
+    Out out;
+    lane_setup<T>(p, warp, lane, g, ct, out, K);
     RegSource<T> src;
-    run_strip<T, K, CLAMP>(p, g, ct, src);
+    run_strip<T, K, CLAMP>(p, g, ct, out, src);
 }
 
 template <typename T, int K, bool CLAMP>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_ring_kernel(const PassArgs p) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, kRingMinBlocks) level_pass_ring_kernel(const PassArgs p) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -527,49 +587,227 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_ring_kernel
     if (warp >= p.n_warps) return;
     LaneGeo g;
     Ctl ct;
-    lane_setup(p, warp, lane, g, ct, K);
+    Out out;
+    lane_setup<T>(p, warp, lane, g, ct, out, K);
 
     RingSource<T> src;
     src.lane = lane;
-    src.slots = smem + (size_t)wib * kRingSlots * p.slot_bytes;
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(
-        smem + (size_t)kWarpsPerBlock * kRingSlots * p.slot_bytes) + wib * kRingSlots;
-    src.bar0 = smem_addr(bars);
-    src.issued = 0;
+    src.slots_s = smem_addr(smem) + (uint32_t)(wib * kRingSlots * p.slot_bytes);
+    src.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * kRingSlots * p.slot_bytes) +
+               8u * (uint32_t)(wib * kRingSlots);
+    src.fslot = src.gslot = 0;
+    src.fpar = src.gpar = 0;
+    src.issued = src.parity = 0;
     // the warp's source column ranges: lanes load columns [xf, xl] of the level
     const int X0 = g.x - 2 * lane;
     const int xf = min(max(X0, 0), p.w - 1);
     const int xl = min(max(X0 + kLaneCols - 1, 0), p.w - 1);
-    src.giF = nearest_src(xf, p.Iw, p.w);
-    src.nI = nearest_src(xl, p.Iw, p.w) - src.giF + 1;
-    src.gsF = nearest_src(xf, p.sw, p.w);
-    src.nS = nearest_src(xl, p.sw, p.w) - src.gsF + 1;
-    src.li = 3 * (g.gi0 - src.giF);
-    src.la = g.gi0 - src.giF;
-    src.ls = 3 * (g.gs0 - src.gsF);
+    const int giF = nearest_src(xf, p.Iw, p.w);
+    const int nI = nearest_src(xl, p.Iw, p.w) - giF + 1;
+    const int gsF = nearest_src(xf, p.sw, p.w);
+    const int nS = nearest_src(xl, p.sw, p.w) - gsF + 1;
+    const int es = (int)sizeof(T);
+    src.colI = 3 * giF * es;
+    src.colA = giF * es;
+    src.colS = 3 * gsF * es;
+    src.lenI = 3 * nI * es;
+    src.lenA = nI * es;
+    src.lenS = 3 * nS * es;
+    src.li = 3 * (g.gi0 - giF);
+    src.la = g.gi0 - giF;
+    src.ls = 3 * (g.gs0 - gsF);
     src.dI = g.gi1 - g.gi0;
     src.dS = g.gs1 - g.gs0;
-    src.parity = 0;
-    const int es = (int)sizeof(T);
-    const unsigned char *Ib = static_cast<const unsigned char *>(p.I);
-    const unsigned char *Ab = static_cast<const unsigned char *>(p.A);
-    const unsigned char *Fb = static_cast<const unsigned char *>(p.Fs);
-    const unsigned char *Bb = static_cast<const unsigned char *>(p.Bs);
-    src.lo[0] = Ib;
-    src.hi[0] = Ib + ((long long)(p.Ih - 1) * p.I_pitch + 3LL * p.Iw) * es;
-    src.lo[1] = Ab;
-    src.hi[1] = Ab + ((long long)(p.Ih - 1) * p.A_pitch + p.Iw) * es;
-    src.lo[2] = Fb;
-    src.hi[2] = Fb + ((long long)(p.sh - 1) * p.s_pitch + 3LL * p.sw) * es;
-    src.lo[3] = Bb;
-    src.hi[3] = Bb + ((long long)(p.sh - 1) * p.s_pitch + 3LL * p.sw) * es;
     if (lane == 0) {
         for (int s = 0; s < kRingSlots; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(src.bar0 + 8u * s) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
-    run_strip<T, K, CLAMP>(p, g, ct, src);
+    run_strip<T, K, CLAMP>(p, g, ct, out, src);
+}
+
+// Tile variant (top level, where I and alpha are the input itself): the warp's rows
+// arrive in chunks of kTileRows rows, each chunk fetched by four 2D tensor copies (boxes
+// of I, alpha, F and B rows; the hardware forms the addresses and fills zeros outside the
+// images), kTileSlots chunks in flight per warp. Ring bookkeeping is paid once per chunk.
+template <typename T>
+struct TileSource {
+    uint32_t slots_s, bar0;
+    int lane;
+    const CUtensorMap *mI, *mA, *mF, *mB;
+    int xI, xA, xS;         // box x coordinates (elements; multiples of 16 bytes)
+    int li, la, ls, dI, dS; // per-lane element offsets inside box rows
+    int r_first;
+    int cfill;              // next chunk to fill
+    int j;                  // row of the current chunk being taken
+    int gslot;              // slot of the current chunk
+    uint32_t gpar;
+    int sy0;                // first source F/B row of the current chunk
+    uint32_t issued, parity;
+    RowMap gS;              // source F/B row of the next row to take
+
+    __device__ __forceinline__ void fill(const PassArgs &p) {
+        const int r0 = r_first + cfill * kTileRows;
+        const int slot = cfill % kTileSlots;
+        const uint32_t par = (uint32_t)(cfill / kTileSlots) & 1u;
+        if (lane == 0) {
+            const uint32_t dst = slots_s + (uint32_t)slot * (uint32_t)p.tile_chunk;
+            const uint32_t bar = bar0 + 8u * (uint32_t)slot;
+            const int sy = nearest_src(r0, p.sh, p.h);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         :: "r"(bar), "r"((uint32_t)p.tile_tx) : "memory");
+            tile_copy(dst, mI, xI, r0, bar);
+            tile_copy(dst + (uint32_t)p.tile_offA, mA, xA, r0, bar);
+            tile_copy(dst + (uint32_t)p.tile_offF, mF, xS, sy, bar);
+            tile_copy(dst + (uint32_t)p.tile_offB, mB, xS, sy, bar);
+        }
+        issued |= 1u << slot;
+        parity = (parity & ~(1u << slot)) | (par << slot);
+        ++cfill;
+    }
+
+    __device__ __forceinline__ static void tile_copy(uint32_t dst, const CUtensorMap *m, int x,
+                                                     int y, uint32_t bar) {
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];"
+            :: "r"(dst), "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(bar)
+            : "memory");
+    }
+
+    __device__ __forceinline__ bool wait(int slot, uint32_t par) const {
+        const uint32_t bar = bar0 + 8u * (uint32_t)slot;
+        uint32_t ok = 0;
+        for (int i = 0; i < kWaitPolls && !ok; ++i) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(ok) : "r"(bar), "r"(par), "r"(kWaitHintNs) : "memory");
+        }
+        return __all_sync(kFull, ok != 0);
+    }
+
+    __device__ __forceinline__ void start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
+        r_first = ct.r_first;
+        cfill = 0;
+        j = 0;
+        gslot = 0;
+        gpar = 0;
+        issued = parity = 0;
+        gS.init(ct.r_first, p.sh, p.h);
+        const int nchunks = (ct.r_last - ct.r_first) / kTileRows + 1;
+        for (int c = 0; c < kTileSlots && c < nchunks; ++c) fill(p);
+    }
+
+    template <typename U>
+    __device__ __forceinline__ static float lds(uint32_t a) {
+        if (sizeof(U) == 4) {
+            float v;
+            asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+            return v;
+        } else {
+            unsigned short u;
+            asm volatile("ld.shared.b16 %0, [%1];" : "=h"(u) : "r"(a) : "memory");
+            U v;
+            *reinterpret_cast<unsigned short *>(&v) = u;
+            return to_f(v);
+        }
+    }
+
+    __device__ __forceinline__ bool get(const PassArgs &p, const LaneGeo &g, const Ctl &ct, int r,
+                                        Raw &o) {
+        if (j == 0) {
+            if (!wait(gslot, gpar)) return false;
+            issued &= ~(1u << gslot);
+            sy0 = nearest_src(r, p.sh, p.h);
+        }
+        const int es = (int)sizeof(T);
+        const int sy = gS.next();
+        const uint32_t base = slots_s + (uint32_t)gslot * (uint32_t)p.tile_chunk;
+        const uint32_t I = base + (uint32_t)((j * p.tile_bwI + li) * es);
+        const uint32_t A = base + (uint32_t)p.tile_offA + (uint32_t)((j * p.tile_bwA + la) * es);
+        const uint32_t F = base + (uint32_t)p.tile_offF + (uint32_t)(((sy - sy0) * p.tile_bwS + ls) * es);
+        const uint32_t B = base + (uint32_t)p.tile_offB + (uint32_t)(((sy - sy0) * p.tile_bwS + ls) * es);
+        o.a0 = lds<T>(A);
+        o.a1 = lds<T>(A + dI * es);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o.i0[c] = lds<T>(I + c * es);
+            o.i1[c] = lds<T>(I + (3 * dI + c) * es);
+            o.f0[c] = lds<T>(F + c * es);
+            o.f1[c] = lds<T>(F + (3 * dS + c) * es);
+            o.b0[c] = lds<T>(B + c * es);
+            o.b1[c] = lds<T>(B + (3 * dS + c) * es);
+        }
+        if (++j == kTileRows || r == ct.r_last) {
+            // the chunk is used up: refill its slot with the chunk kTileSlots ahead
+            __syncwarp();
+            j = 0;
+            if (r_first + cfill * kTileRows <= ct.r_last) fill(p);
+            if (++gslot == kTileSlots) {
+                gslot = 0;
+                gpar ^= 1u;
+            }
+        }
+        return true;
+    }
+
+    __device__ __forceinline__ void abort() const {
+        for (int s = 0; s < kTileSlots; ++s)
+            if (issued & (1u << s)) wait(s, (parity >> s) & 1u);
+    }
+};
+
+template <typename T, int K, bool CLAMP>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_tile_kernel(
+    const PassArgs p, const __grid_constant__ CUtensorMap mI, const __grid_constant__ CUtensorMap mA,
+    const __grid_constant__ CUtensorMap mF, const __grid_constant__ CUtensorMap mB) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (warp >= p.n_warps) return;
+    LaneGeo g;
+    Ctl ct;
+    Out out;
+    lane_setup<T>(p, warp, lane, g, ct, out, K);
+
+    TileSource<T> src;
+    src.lane = lane;
+    src.mI = &mI;
+    src.mA = &mA;
+    src.mF = &mF;
+    src.mB = &mB;
+    src.slots_s = smem_addr(smem) + (uint32_t)(wib * kTileSlots * p.tile_chunk);
+    src.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * kTileSlots * p.tile_chunk) +
+               8u * (uint32_t)(wib * kTileSlots);
+    // box x coordinates: the strip's first column rounded down to 16 bytes (may be
+    // negative; the copy then fills zeros there)
+    const int q = 16 / (int)sizeof(T);
+    const int X0 = g.x - 2 * lane;
+    auto floor_q = [q](int v) { return v >= 0 ? v / q * q : -((-v + q - 1) / q) * q; };
+    src.xI = floor_q(3 * X0);
+    src.xA = floor_q(X0);
+    const int xf = min(max(X0, 0), p.w - 1);
+    const int gsF = nearest_src(xf, p.sw, p.w);
+    src.xS = floor_q(3 * gsF);
+    // the lanes read their own columns; outside the image those are zero-filled
+    // (weights ignore them)
+    src.li = 3 * g.x - src.xI;
+    src.la = g.x - src.xA;
+    src.dI = 1;
+    src.ls = 3 * g.gs0 - src.xS;
+    src.dS = g.gs1 - g.gs0;
+    if (lane == 0) {
+        for (int s = 0; s < kTileSlots; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(src.bar0 + 8u * s) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    run_strip<T, K, CLAMP>(p, g, ct, out, src);
 }
 
 // Zero sweeps: the level's F and B are the nearest resize of the starting state.
@@ -607,6 +845,25 @@ cudaError_t launch_ring_t(const PassArgs &a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     level_pass_ring_kernel<T, K, CLAMP><<<blocks, kWarpsPerBlock * 32, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, int K, bool CLAMP>
+cudaError_t launch_tile_t(const PassArgs &a, const TileMaps &m, cudaStream_t s) {
+    const int blocks = (a.n_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const size_t smem = level_pass_tile_smem(a.tile_chunk);
+    cudaError_t e = cudaFuncSetAttribute(level_pass_tile_kernel<T, K, CLAMP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    level_pass_tile_kernel<T, K, CLAMP><<<blocks, kWarpsPerBlock * 32, smem, s>>>(a, m.I, m.A, m.F, m.B);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tile_dtype(int iters, int clamp, const PassArgs &a, const TileMaps &m,
+                              cudaStream_t s) {
+    if (iters == 1) return clamp ? launch_tile_t<T, 1, true>(a, m, s) : launch_tile_t<T, 1, false>(a, m, s);
+    if (iters == 2) return clamp ? launch_tile_t<T, 2, true>(a, m, s) : launch_tile_t<T, 2, false>(a, m, s);
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -653,6 +910,23 @@ cudaError_t launch_level_pass_ring(int dtype, int iters, int clamp, const PassAr
     }
     return cudaErrorInvalidValue;
 }
+
+cudaError_t launch_level_pass_tile(int dtype, int iters, int clamp, const PassArgs &a,
+                                   const TileMaps &m, cudaStream_t s) {
+    switch (dtype) {
+        case kF32: return launch_tile_dtype<float>(iters, clamp, a, m, s);
+        case kBF16: return launch_tile_dtype<__nv_bfloat16>(iters, clamp, a, m, s);
+        case kF16: return launch_tile_dtype<__half>(iters, clamp, a, m, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+size_t level_pass_tile_smem(int chunk_bytes) {
+    return (size_t)kWarpsPerBlock * kTileSlots * (size_t)chunk_bytes +
+           (size_t)kWarpsPerBlock * kTileSlots * 8;
+}
+
+int level_pass_tile_rows() { return kTileRows; }
 
 size_t level_pass_ring_smem(int slot_bytes) {
     return (size_t)kWarpsPerBlock * kRingSlots * (size_t)slot_bytes +

@@ -79,7 +79,10 @@ def test_parameters(fgml, kw):
 
 @pytest.mark.parametrize("iters", [0, 1, 2, 3, 4, 7])
 @pytest.mark.parametrize("w,h,sw,sh,Iw,Ih", [(130, 70, 66, 35, 260, 140), (61, 200, 61, 200, 61, 200),
-                                             (500, 9, 251, 5, 1001, 17), (7, 3, 2, 2, 7, 3)])
+                                             (500, 9, 251, 5, 1001, 17), (7, 3, 2, 2, 7, 3),
+                                             (128, 96, 64, 48, 128, 96),
+                                             (200, 100, 200, 100, 200, 100),
+                                             (1000, 37, 497, 19, 1000, 37)])
 def test_level_pass_against_oracle_sweeps(fgml, iters, w, h, sw, sh, Iw, Ih):
     rng = np.random.default_rng(iters * 100 + w)
     I = rng.random((Ih, Iw, 3)).astype(np.float32)
