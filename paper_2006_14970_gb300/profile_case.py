@@ -37,8 +37,11 @@ def main():
         levels = fgml.schedule(a.w, a.h)
         (pw, ph, _), (_, _, k) = levels[-2], levels[-1]
         g = torch.Generator(device="cuda").manual_seed(1)
-        Fs = torch.rand((ph, pw, 3), device="cuda", generator=g).to(dt)
-        Bs = torch.rand((ph, pw, 3), device="cuda", generator=g).to(dt)
+        # rows padded to 16 bytes, like the library's own intermediate levels
+        q = 16 // torch.empty((), dtype=dt).element_size()
+        pitch = (3 * pw + q - 1) // q * q
+        Fs = torch.rand((ph, pitch), device="cuda", generator=g).to(dt)[:, :3 * pw].view(ph, pw, 3)
+        Bs = torch.rand((ph, pitch), device="cuda", generator=g).to(dt)[:, :3 * pw].view(ph, pw, 3)
         F = torch.empty_like(I)
         B = torch.empty_like(I)
         def run():
