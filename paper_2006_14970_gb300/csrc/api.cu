@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -145,7 +146,18 @@ struct Buf {
 struct Workspace {
     Buf lev[2];   // intermediate level states: F then B, each w x h x 3
     Buf stage;    // device staging of the host-memory entry point
+    // launch sequences of fg_estimate captured as CUDA graphs, by call signature
+    std::map<std::string, cudaGraphExec_t> graphs;
+    std::vector<std::string> graph_order;   // oldest first, for eviction
 };
+
+constexpr size_t kMaxGraphs = 64;   // cached launch graphs per workspace
+
+void clear_graphs(Workspace &ws) {
+    for (auto &kv : ws.graphs) cudaGraphExecDestroy(kv.second);
+    ws.graphs.clear();
+    ws.graph_order.clear();
+}
 
 std::mutex g_ws_mu;
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
@@ -396,29 +408,11 @@ fg_status run_level(int dtype, const fg_params &p, const Input &in, State &src, 
     return FG_OK;
 }
 
-fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, void *Bd,
-                   long long d_pitch, cudaStream_t s) {
-    const int es = dtype == kF32 ? 4 : 2;
-    const std::vector<Level> lv = plan_levels(in.w, in.h, p);
+// The kernels of one solve, enqueued on `s` (no allocation, no synchronisation).
+fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
+                          const std::vector<Level> &lv, int nc, void *Fd, void *Bd,
+                          long long d_pitch, Workspace &ws, int es, cudaStream_t s) {
     const int n = (int)lv.size();
-    const int nc = coarse_levels(lv);   // levels run by the coarse kernel
-
-    // workspace: every intermediate state, including extra passes of the top level
-    size_t need = 0;
-    if (nc < n) need = state_bytes(lv[nc - 1].w, lv[nc - 1].h, es);
-    for (int l = nc; l < n; ++l) {
-        const bool top = l == n - 1;
-        if (!top || split_sweeps(lv[l].k).size() > 1)
-            need = std::max(need, state_bytes(lv[l].w, lv[l].h, es));
-    }
-    Workspace &ws = workspace_for(s);
-    if (need) {
-        fg_status st = ensure(ws.lev[0], need, s);
-        if (st != FG_OK) return st;
-        st = ensure(ws.lev[1], need, s);
-        if (st != FG_OK) return st;
-    }
-
     CoarseArgs ca;
     std::memset(&ca, 0, sizeof ca);
     ca.I = in.I;
@@ -459,6 +453,109 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
                                  Fd, Bd, d_pitch, ws, es, s);
         if (st != FG_OK) return st;
     }
+    return FG_OK;
+}
+
+// Per-device stream on which launch sequences are captured into graphs.
+cudaStream_t capture_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    const int d = current_device();
+    if (d < 0 || d >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!streams[d] && cudaStreamCreateWithFlags(&streams[d], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[d] = nullptr;
+    }
+    return streams[d];
+}
+
+bool graphs_enabled() {
+    static const bool on = [] {
+        const char *v = std::getenv("FGML_NO_GRAPH");
+        return !(v && *v && *v != '0');
+    }();
+    return on;
+}
+
+fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, void *Bd,
+                   long long d_pitch, cudaStream_t s) {
+    const int es = dtype == kF32 ? 4 : 2;
+    const std::vector<Level> lv = plan_levels(in.w, in.h, p);
+    const int n = (int)lv.size();
+    const int nc = coarse_levels(lv);   // levels run by the coarse kernel
+
+    // workspace: every intermediate state, including extra passes of the top level
+    size_t need = 0;
+    if (nc < n) need = state_bytes(lv[nc - 1].w, lv[nc - 1].h, es);
+    for (int l = nc; l < n; ++l) {
+        const bool top = l == n - 1;
+        if (!top || split_sweeps(lv[l].k).size() > 1)
+            need = std::max(need, state_bytes(lv[l].w, lv[l].h, es));
+    }
+    Workspace &ws = workspace_for(s);
+    if (need && (ws.lev[0].bytes < need || ws.lev[1].bytes < need)) {
+        // cached graphs point at the buffers about to be replaced
+        cudaStreamSynchronize(s);
+        clear_graphs(ws);
+        fg_status st = ensure(ws.lev[0], need, s);
+        if (st != FG_OK) return st;
+        st = ensure(ws.lev[1], need, s);
+        if (st != FG_OK) return st;
+    }
+    if (!graphs_enabled())
+        return launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s);
+
+    // the launch sequence depends on the pointers, pitches, sizes, dtype and parameters
+    struct {
+        const void *I, *A;
+        void *F, *B;
+        long long Ip, Ap, dp;
+        int w, h, dtype;
+        fg_params p;
+    } sig;
+    std::memset(&sig, 0, sizeof sig);
+    sig.I = in.I;
+    sig.A = in.A;
+    sig.F = Fd;
+    sig.B = Bd;
+    sig.Ip = in.I_pitch;
+    sig.Ap = in.A_pitch;
+    sig.dp = d_pitch;
+    sig.w = in.w;
+    sig.h = in.h;
+    sig.dtype = dtype;
+    sig.p = p;
+    const std::string key(reinterpret_cast<const char *>(&sig), sizeof sig);
+    auto it = ws.graphs.find(key);
+    if (it == ws.graphs.end()) {
+        cudaStream_t cs = capture_stream();
+        if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s);
+        }
+        fg_status st = launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, cs);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (st != FG_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "capturing the launch sequence");
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "instantiating the launch graph");
+        if (ws.graphs.size() >= kMaxGraphs) {
+            cudaGraphExecDestroy(ws.graphs[ws.graph_order.front()]);
+            ws.graphs.erase(ws.graph_order.front());
+            ws.graph_order.erase(ws.graph_order.begin());
+        }
+        it = ws.graphs.emplace(key, ex).first;
+        ws.graph_order.push_back(key);
+    }
+    cudaError_t e = cudaGraphLaunch(it->second, s);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
     return FG_OK;
 }
 
@@ -622,6 +719,7 @@ fg_status fg_release_workspace(void *stream) {
         g_ws.erase(it);
     }
     cudaStreamSynchronize(s);
+    clear_graphs(w);
     cudaFree(w.lev[0].p);
     cudaFree(w.lev[1].p);
     cudaFree(w.stage.p);

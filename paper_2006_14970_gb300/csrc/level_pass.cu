@@ -41,9 +41,8 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kLaneCols = 64;        // columns held by a warp (2 per lane)
 constexpr int kWaitPolls = 1 << 20;          // try_wait polls before a wait gives up
 constexpr uint32_t kWaitHintNs = 2000;       // suspend-time hint of one poll
-constexpr int kTileRows = 3;                 // rows per tensor-copy chunk
-constexpr int kTileSlots = 3;                // chunks resident or in flight per warp
-constexpr int kTileMinBlocks = 3;            // resident blocks per SM the tile kernel targets
+constexpr int kTileRows = 4;                 // rows per tensor-copy chunk
+constexpr int kTileSlots = 3;                // chunks in flight per warp
 #ifndef FGML_RING_MIN_BLOCKS
 #define FGML_RING_MIN_BLOCKS 2
 #endif
@@ -436,19 +435,11 @@ struct RingSource {
         return true;
     }
 
+    const unsigned char *sm;   // the block's shared memory, and its shared address
+    uint32_t sbase;
     template <typename U>
-    __device__ __forceinline__ static float lds(uint32_t a) {
-        if (sizeof(U) == 4) {
-            float v;
-            asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
-            return v;
-        } else {
-            unsigned short u;
-            asm volatile("ld.shared.b16 %0, [%1];" : "=h"(u) : "r"(a) : "memory");
-            U v;
-            *reinterpret_cast<unsigned short *>(&v) = u;
-            return to_f(v);
-        }
+    __device__ __forceinline__ float lds(uint32_t a) const {
+        return to_f(*reinterpret_cast<const U *>(sm + (a - sbase)));
     }
 
     // After a failed wait: wait (bounded) for every fill still in flight, then return.
@@ -592,6 +583,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kRingMinBlocks) level_pas
     lane_setup<T>(p, warp, lane, g, ct, out, K);
 
     RingSource<T> src;
+    src.sm = smem;
+    src.sbase = smem_addr(smem);
     src.lane = lane;
     src.slots_s = smem_addr(smem) + (uint32_t)(wib * kRingSlots * p.slot_bytes);
     src.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * kRingSlots * p.slot_bytes) +
@@ -628,218 +621,134 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kRingMinBlocks) level_pas
     run_strip<T, K, CLAMP>(p, g, ct, out, src);
 }
 
-// Tile variant (top level, where I and alpha are the input itself). The warp's rows
+// Tile variant (top level, where I and alpha are the input itself): the warp's rows
 // arrive in chunks of kTileRows rows, each chunk fetched by four 2D tensor copies (boxes
-// of I, alpha, F and B rows; the hardware forms the addresses and fills zeros outside
-// the images), with kTileSlots chunks resident or in flight per warp. Sweep 1 reads its
-// starting rows straight from the chunks, so a chunk is kept until two rows after its
-// last one; only the row constants and the sweep-1 rows live in registers.
+// of I, alpha, F and B rows; the hardware forms the addresses and fills zeros outside the
+// images), kTileSlots chunks in flight per warp. Ring bookkeeping is paid once per chunk.
 template <typename T>
-__device__ __forceinline__ float lds_elem(uint32_t a) {
-    if (sizeof(T) == 4) {
-        float v;
-        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
-        return v;
-    } else {
-        unsigned short u;
-        asm volatile("ld.shared.b16 %0, [%1];" : "=h"(u) : "r"(a) : "memory");
-        T v;
-        *reinterpret_cast<unsigned short *>(&v) = u;
-        return to_f(v);
-    }
-}
+struct TileSource {
+    uint32_t slots_s, bar0;
+    int lane;
+    const CUtensorMap *mI, *mA, *mF, *mB;
+    int xI, xA, xS;         // box x coordinates (elements; multiples of 16 bytes)
+    int li, la, ls, dI, dS; // per-lane element offsets inside box rows
+    int r_first;
+    int cfill;              // next chunk to fill
+    int j;                  // row of the current chunk being taken
+    int gslot;              // slot of the current chunk
+    uint32_t gpar;
+    int sy0;                // first source F/B row of the current chunk
+    uint32_t issued, parity;
+    RowMap gS;              // source F/B row of the next row to take
 
-template <typename T, bool CLAMP>
-__device__ __forceinline__ void update_smem(const RowK &k, uint32_t aC, uint32_t aU, uint32_t aD,
-                                            uint32_t dFB, int dS, FB &out) {
-    const int es = (int)sizeof(T);
-    const float2 be = f2(1.f - k.a.x, 1.f - k.a.y);
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        const int o = ch * es;
-        const float2 cF = f2(lds_elem<T>(aC + o), lds_elem<T>(aC + dS + o));
-        const float2 cB = f2(lds_elem<T>(aC + dFB + o), lds_elem<T>(aC + dFB + dS + o));
-        const float2 uF = f2(lds_elem<T>(aU + o), lds_elem<T>(aU + dS + o));
-        const float2 uB = f2(lds_elem<T>(aU + dFB + o), lds_elem<T>(aU + dFB + dS + o));
-        const float2 dF = f2(lds_elem<T>(aD + o), lds_elem<T>(aD + dS + o));
-        const float2 dB = f2(lds_elem<T>(aD + dFB + o), lds_elem<T>(aD + dFB + dS + o));
-        const float lF = __shfl_up_sync(kFull, cF.y, 1);
-        const float rF = __shfl_down_sync(kFull, cF.x, 1);
-        const float lB = __shfl_up_sync(kFull, cB.y, 1);
-        const float rB = __shfl_down_sync(kFull, cB.x, 1);
-        float2 sF = fma2(k.ws, cF, mul2(k.wu, uF));
-        sF = fma2(k.wl, f2(lF, cF.x), sF);
-        sF = fma2(k.wr, f2(cF.y, rF), sF);
-        sF = fma2(k.wd, dF, sF);
-        float2 sB = fma2(k.ws, cB, mul2(k.wu, uB));
-        sB = fma2(k.wl, f2(lB, cB.x), sB);
-        sB = fma2(k.wr, f2(cB.y, rB), sB);
-        sB = fma2(k.wd, dB, sB);
-        const float2 bF = fma2(k.a, k.I[ch], sF);
-        const float2 bB = fma2(be, k.I[ch], sB);
-        const float2 tF = mul2(k.nFB, bB);
-        const float2 tB = mul2(k.nFB, bF);
-        if (CLAMP) {
-            out.F[ch] = f2(__saturatef(fmaf(k.mFF.x, bF.x, tF.x)), __saturatef(fmaf(k.mFF.y, bF.y, tF.y)));
-            out.B[ch] = f2(__saturatef(fmaf(k.mBB.x, bB.x, tB.x)), __saturatef(fmaf(k.mBB.y, bB.y, tB.y)));
-        } else {
-            out.F[ch] = fma2(k.mFF, bF, tF);
-            out.B[ch] = fma2(k.mBB, bB, tB);
+    __device__ __forceinline__ void fill(const PassArgs &p) {
+        const int r0 = r_first + cfill * kTileRows;
+        const int slot = cfill % kTileSlots;
+        const uint32_t par = (uint32_t)(cfill / kTileSlots) & 1u;
+        if (lane == 0) {
+            const uint32_t dst = slots_s + (uint32_t)slot * (uint32_t)p.tile_chunk;
+            const uint32_t bar = bar0 + 8u * (uint32_t)slot;
+            const int sy = nearest_src(r0, p.sh, p.h);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         :: "r"(bar), "r"((uint32_t)p.tile_tx) : "memory");
+            tile_copy(dst, mI, xI, r0, bar);
+            tile_copy(dst + (uint32_t)p.tile_offA, mA, xA, r0, bar);
+            tile_copy(dst + (uint32_t)p.tile_offF, mF, xS, sy, bar);
+            tile_copy(dst + (uint32_t)p.tile_offB, mB, xS, sy, bar);
         }
+        issued |= 1u << slot;
+        parity = (parity & ~(1u << slot)) | (par << slot);
+        ++cfill;
     }
-}
 
-struct TileRow {            // where a row's data sits in the chunk ring (shared addresses)
-    uint32_t F;             // F of the lane's first pixel in the row's source F/B row
-    uint32_t A;             // alpha of the lane's first pixel
-    uint32_t I;             // I of the lane's first pixel
-    bool last;              // last row of its chunk
-};
-
-struct TileCtx {
-    uint32_t slots, bar0;   // shared addresses of the warp's chunk slots and mbarriers
-    uint32_t offI, offA, offS;   // lane byte offsets inside box rows
-    uint32_t dFB;           // bytes from a chunk's F box to its B box
-    int dS;                 // bytes from the lane's first to second pixel in an F/B row
-    int xI, xA, xS;         // box x coordinates (elements)
-    int nchunks;
-    int cur_c;              // chunk of the newest row taken
-    int j;                  // its row inside the chunk
-    int sy0;                // first F/B source row of that chunk
-    RowMap gS;              // F/B source row of the next row to take
-};
-
-template <typename T>
-__device__ __forceinline__ void tile_fill(const PassArgs &p, const TileCtx &t, int c, int r_first,
-                                          const CUtensorMap *mI, const CUtensorMap *mA,
-                                          const CUtensorMap *mF, const CUtensorMap *mB) {
-    if ((threadIdx.x & 31) != 0) return;
-    const int r0 = r_first + c * kTileRows;
-    const int slot = c % kTileSlots;
-    const uint32_t dst = t.slots + (uint32_t)slot * (uint32_t)p.tile_chunk;
-    const uint32_t bar = t.bar0 + 8u * (uint32_t)slot;
-    const int sy = nearest_src(r0, p.sh, p.h);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(bar), "r"((uint32_t)p.tile_tx) : "memory");
-#define FGML_TILE_COPY(D, M, X, Y)                                                          \
-    asm volatile(                                                                            \
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"   \
-        " [%0], [%1, {%2, %3}], [%4];"                                                       \
-        :: "r"(D), "l"(reinterpret_cast<uint64_t>(M)), "r"(X), "r"(Y), "r"(bar) : "memory")
-    FGML_TILE_COPY(dst, mI, t.xI, r0);
-    FGML_TILE_COPY(dst + (uint32_t)p.tile_offA, mA, t.xA, r0);
-    FGML_TILE_COPY(dst + (uint32_t)p.tile_offF, mF, t.xS, sy);
-    FGML_TILE_COPY(dst + (uint32_t)p.tile_offB, mB, t.xS, sy);
-#undef FGML_TILE_COPY
-}
-
-__device__ __forceinline__ bool tile_wait(const TileCtx &t, int c) {
-    const uint32_t bar = t.bar0 + 8u * (uint32_t)(c % kTileSlots);
-    const uint32_t par = (uint32_t)(c / kTileSlots) & 1u;
-    uint32_t ok = 0;
-    for (int i = 0; i < kWaitPolls && !ok; ++i) {
+    __device__ __forceinline__ static void tile_copy(uint32_t dst, const CUtensorMap *m, int x,
+                                                     int y, uint32_t bar) {
         asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok) : "r"(bar), "r"(par), "r"(kWaitHintNs) : "memory");
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];"
+            :: "r"(dst), "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(bar)
+            : "memory");
     }
-    return __all_sync(kFull, ok != 0);
-}
 
-// Builds the constants of row q (alpha, I, weights, A^{-1}); `above` holds row q-1's.
-template <typename T>
-__device__ __forceinline__ void tile_row_consts(const PassArgs &p, const LaneGeo &g, int q,
-                                                const TileRow &rq, const TileRow &rq1, bool have_below,
-                                                const RowK &above, RowK &k) {
-    const int es = (int)sizeof(T);
-    Raw raw;
-    raw.a0 = lds_elem<T>(rq.A);
-    raw.a1 = lds_elem<T>(rq.A + es);
+    __device__ __forceinline__ bool wait(int slot, uint32_t par) const {
+        const uint32_t bar = bar0 + 8u * (uint32_t)slot;
+        uint32_t ok = 0;
+        for (int i = 0; i < kWaitPolls && !ok; ++i) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(ok) : "r"(bar), "r"(par), "r"(kWaitHintNs) : "memory");
+        }
+        return __all_sync(kFull, ok != 0);
+    }
+
+    __device__ __forceinline__ void start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
+        r_first = ct.r_first;
+        cfill = 0;
+        j = 0;
+        gslot = 0;
+        gpar = 0;
+        issued = parity = 0;
+        gS.init(ct.r_first, p.sh, p.h);
+        const int nchunks = (ct.r_last - ct.r_first) / kTileRows + 1;
+        for (int c = 0; c < kTileSlots && c < nchunks; ++c) fill(p);
+    }
+
+    const unsigned char *sm;   // the block's shared memory, and its shared address
+    uint32_t sbase;
+    template <typename U>
+    __device__ __forceinline__ float lds(uint32_t a) const {
+        return to_f(*reinterpret_cast<const U *>(sm + (a - sbase)));
+    }
+
+    __device__ __forceinline__ bool get(const PassArgs &p, const LaneGeo &g, const Ctl &ct, int r,
+                                        Raw &o) {
+        if (j == 0) {
+            if (!wait(gslot, gpar)) return false;
+            issued &= ~(1u << gslot);
+            sy0 = nearest_src(r, p.sh, p.h);
+        }
+        const int es = (int)sizeof(T);
+        const int sy = gS.next();
+        const uint32_t base = slots_s + (uint32_t)gslot * (uint32_t)p.tile_chunk;
+        const uint32_t I = base + (uint32_t)((j * p.tile_bwI + li) * es);
+        const uint32_t A = base + (uint32_t)p.tile_offA + (uint32_t)((j * p.tile_bwA + la) * es);
+        const uint32_t F = base + (uint32_t)p.tile_offF + (uint32_t)(((sy - sy0) * p.tile_bwS + ls) * es);
+        const uint32_t B = base + (uint32_t)p.tile_offB + (uint32_t)(((sy - sy0) * p.tile_bwS + ls) * es);
+        o.a0 = lds<T>(A);
+        o.a1 = lds<T>(A + dI * es);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        raw.i0[c] = lds_elem<T>(rq.I + c * es);
-        raw.i1[c] = lds_elem<T>(rq.I + (3 + c) * es);
-        raw.f0[c] = raw.f1[c] = raw.b0[c] = raw.b1[c] = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            o.i0[c] = lds<T>(I + c * es);
+            o.i1[c] = lds<T>(I + (3 * dI + c) * es);
+            o.f0[c] = lds<T>(F + c * es);
+            o.f1[c] = lds<T>(F + (3 * dS + c) * es);
+            o.b0[c] = lds<T>(B + c * es);
+            o.b1[c] = lds<T>(B + (3 * dS + c) * es);
+        }
+        if (++j == kTileRows || r == ct.r_last) {
+            // the chunk is used up: refill its slot with the chunk kTileSlots ahead
+            __syncwarp();
+            j = 0;
+            if (r_first + cfill * kTileRows <= ct.r_last) fill(p);
+            if (++gslot == kTileSlots) {
+                gslot = 0;
+                gpar ^= 1u;
+            }
+        }
+        return true;
     }
-    FB unused;
-    make_row(raw, g, q, above, p.eps, p.omega, k, unused);
-    if (q < p.h - 1) {
-        const float b0 = have_below ? lds_elem<T>(rq1.A) : raw.a0;
-        const float b1 = have_below ? lds_elem<T>(rq1.A + es) : raw.a1;
-        k.wd = f2(edge_w(raw.a0, b0, p.eps, p.omega), edge_w(raw.a1, b1, p.eps, p.omega));
-    } else {
-        k.wd = f2(0.f, 0.f);
-        k.ws = add2(k.ws, f2(p.eps, p.eps));
-    }
-    finish_row(k);
-}
 
-// One row step of the tile variant: take row r, build the constants of row r-1, sweep 1
-// at row r-1 (starting rows read from the chunks), sweep 2 at row r-2, release the
-// chunk of row r-2 if that was its last row. Rn/R1/R2: ring positions of rows r, r-1,
-// r-2; S1/S2: constants of rows r-1, r-2 (S2 also serves as "above" for row r-1);
-// P: sweep-1 rows r-1 (written), r-2, r-3.
-template <typename T, int K, bool CLAMP>
-__device__ __forceinline__ bool tile_step(const PassArgs &p, const LaneGeo &g, const Ctl &ct,
-                                          const Out &out, TileCtx &t, int r, TileRow &Rn,
-                                          const TileRow &R1, const TileRow &R2, RowK &S1,
-                                          const RowK &S2, FB &Pw, const FB &Pr2, const FB &Pr3,
-                                          const CUtensorMap *mI, const CUtensorMap *mA,
-                                          const CUtensorMap *mF, const CUtensorMap *mB) {
-    const int es = (int)sizeof(T);
-    if (r <= ct.r_last) {
-        if (t.j == kTileRows) {
-            t.j = 0;
-            ++t.cur_c;
-        }
-        if (t.j == 0) {
-            if (!tile_wait(t, t.cur_c)) return false;
-            t.sy0 = nearest_src(r, p.sh, p.h);
-        }
-        const uint32_t base = t.slots + (uint32_t)(t.cur_c % kTileSlots) * (uint32_t)p.tile_chunk;
-        const int sy = t.gS.next();
-        Rn.I = base + (uint32_t)(t.j * p.tile_bwI * es) + t.offI;
-        Rn.A = base + (uint32_t)p.tile_offA + (uint32_t)(t.j * p.tile_bwA * es) + t.offA;
-        Rn.F = base + (uint32_t)p.tile_offF + (uint32_t)((sy - t.sy0) * p.tile_bwS * es) + t.offS;
-        Rn.last = t.j == kTileRows - 1 || r == ct.r_last;
-        ++t.j;
+    __device__ __forceinline__ void abort() const {
+        for (int s = 0; s < kTileSlots; ++s)
+            if (issued & (1u << s)) wait(s, (parity >> s) & 1u);
     }
-    const int q = r - 1;
-    if (q >= ct.r_first && q <= ct.r_last)
-        tile_row_consts<T>(p, g, q, R1, Rn, q < ct.r_last, S2, S1);
-    if (K == 1) {
-        if (q >= ct.Y0 && q < ct.Y1) {
-            FB res;
-            update_smem<T, CLAMP>(S1, R1.F, q > 0 ? R2.F : R1.F, q < p.h - 1 ? Rn.F : R1.F,
-                                  t.dFB, t.dS, res);
-            store_row<T>(out, q, res);
-        }
-    } else {
-        if (q >= ct.t1_lo && q <= ct.t1_hi) {
-            update_smem<T, CLAMP>(S1, R1.F, q > 0 ? R2.F : R1.F, q < p.h - 1 ? Rn.F : R1.F,
-                                  t.dFB, t.dS, Pw);
-        }
-        const int q2 = r - 2;
-        if (q2 >= ct.Y0 && q2 < ct.Y1) {
-            FB res;
-            update<CLAMP>(S2, Pr2, Pr3, Pw, res);
-            store_row<T>(out, q2, res);
-        }
-    }
-    // row r-2 is no longer read: if it closed its chunk, refill that slot
-    const int q2 = r - 2;
-    if (q2 >= ct.r_first && q2 <= ct.r_last && R2.last) {
-        const int c = (q2 - ct.r_first) / kTileRows + kTileSlots;
-        __syncwarp();
-        if (c < t.nchunks) tile_fill<T>(p, t, c, ct.r_first, mI, mA, mF, mB);
-    }
-    return true;
-}
+};
 
 template <typename T, int K, bool CLAMP>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, kTileMinBlocks) level_pass_tile_kernel(
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_tile_kernel(
     const PassArgs p, const __grid_constant__ CUtensorMap mI, const __grid_constant__ CUtensorMap mA,
     const __grid_constant__ CUtensorMap mF, const __grid_constant__ CUtensorMap mB) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -851,61 +760,42 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kTileMinBlocks) level_pas
     Ctl ct;
     Out out;
     lane_setup<T>(p, warp, lane, g, ct, out, K);
-    const int es = (int)sizeof(T);
 
-    TileCtx t;
-    t.slots = smem_addr(smem) + (uint32_t)(wib * kTileSlots * p.tile_chunk);
-    t.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * kTileSlots * p.tile_chunk) +
-             8u * (uint32_t)(wib * kTileSlots);
+    TileSource<T> src;
+    src.sm = smem;
+    src.sbase = smem_addr(smem);
+    src.lane = lane;
+    src.mI = &mI;
+    src.mA = &mA;
+    src.mF = &mF;
+    src.mB = &mB;
+    src.slots_s = smem_addr(smem) + (uint32_t)(wib * kTileSlots * p.tile_chunk);
+    src.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * kTileSlots * p.tile_chunk) +
+               8u * (uint32_t)(wib * kTileSlots);
     // box x coordinates: the strip's first column rounded down to 16 bytes (may be
-    // negative; the copy then fills zeros there). Lanes read their own columns; outside
-    // the image those are zeros, which the weights ignore.
-    const int qd = 16 / es;
+    // negative; the copy then fills zeros there)
+    const int q = 16 / (int)sizeof(T);
     const int X0 = g.x - 2 * lane;
-    auto floor_q = [qd](int v) { return v >= 0 ? v / qd * qd : -((-v + qd - 1) / qd) * qd; };
-    t.xI = floor_q(3 * X0);
-    t.xA = floor_q(X0);
+    auto floor_q = [q](int v) { return v >= 0 ? v / q * q : -((-v + q - 1) / q) * q; };
+    src.xI = floor_q(3 * X0);
+    src.xA = floor_q(X0);
     const int xf = min(max(X0, 0), p.w - 1);
-    t.xS = floor_q(3 * nearest_src(xf, p.sw, p.w));
-    t.offI = (uint32_t)((3 * g.x - t.xI) * es);
-    t.offA = (uint32_t)((g.x - t.xA) * es);
-    t.offS = (uint32_t)((3 * g.gs0 - t.xS) * es);
-    t.dS = 3 * (g.gs1 - g.gs0) * es;
-    t.dFB = (uint32_t)(p.tile_offB - p.tile_offF);
-    t.nchunks = (ct.r_last - ct.r_first) / kTileRows + 1;
-    t.cur_c = 0;
-    t.j = 0;
-    t.sy0 = 0;
-    t.gS.init(ct.r_first, p.sh, p.h);
+    const int gsF = nearest_src(xf, p.sw, p.w);
+    src.xS = floor_q(3 * gsF);
+    // the lanes read their own columns; outside the image those are zero-filled
+    // (weights ignore them)
+    src.li = 3 * g.x - src.xI;
+    src.la = g.x - src.xA;
+    src.dI = 1;
+    src.ls = 3 * g.gs0 - src.xS;
+    src.dS = g.gs1 - g.gs0;
     if (lane == 0) {
         for (int s = 0; s < kTileSlots; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(t.bar0 + 8u * s) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(src.bar0 + 8u * s) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
-    for (int c = 0; c < kTileSlots && c < t.nchunks; ++c)
-        tile_fill<T>(p, t, c, ct.r_first, &mI, &mA, &mF, &mB);
-
-    TileRow T0, T1, T2;
-    T0 = T1 = T2 = TileRow{0u, 0u, 0u, false};
-    RowK S0, S1, S2;
-    FB P0, P1, P2;
-    zero(S0); zero(S1); zero(S2);
-    zero(P0); zero(P1); zero(P2);
-    const int r_end = ct.r_last + K;
-    bool ok = true;
-    for (int r = ct.r_first; r <= r_end && ok; r += 3) {
-        ok = tile_step<T, K, CLAMP>(p, g, ct, out, t, r, T0, T2, T1, S2, S1, P2, P1, P0, &mI, &mA, &mF, &mB);
-        if (!ok || r + 1 > r_end) break;
-        ok = tile_step<T, K, CLAMP>(p, g, ct, out, t, r + 1, T1, T0, T2, S0, S2, P0, P2, P1, &mI, &mA, &mF, &mB);
-        if (!ok || r + 2 > r_end) break;
-        ok = tile_step<T, K, CLAMP>(p, g, ct, out, t, r + 2, T2, T1, T0, S1, S0, P1, P0, P2, &mI, &mA, &mF, &mB);
-    }
-    if (!ok) {
-        if (lane == 0) atomicExch(&g_device_error, 1);
-        // wait (bounded) for every chunk that may still be in flight, then return
-        for (int c = t.cur_c; c < t.nchunks && c < t.cur_c + kTileSlots; ++c) tile_wait(t, c);
-    }
+    run_strip<T, K, CLAMP>(p, g, ct, out, src);
 }
 
 // Zero sweeps: the level's F and B are the nearest resize of the starting state.
