@@ -251,6 +251,9 @@ int strip_rows(int w, int h) {
     return (int)r;
 }
 
+// Levels up to this many pixels run in the small-level kernel (latency bound).
+constexpr long long kSmallLevelPixels = 300000;
+
 // Shared memory of one ring- or tile-variant block; two blocks must fit on an SM.
 constexpr size_t kRingSmemBudget = 110 * 1024;
 
@@ -350,6 +353,8 @@ cudaError_t pass(int dtype, int iters, int clamp, const fg_params &p, const Inpu
     a.n_xstrips = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
     a.n_warps = a.n_xstrips * ((h + a.strip_h - 1) / a.strip_h);
     a.capI = a.capA = a.capS = a.slot_bytes = 0;
+    if ((iters == 1 || iters == 2) && (long long)w * h <= kSmallLevelPixels)
+        return launch_level_small(dtype, iters, clamp, a, s);
     if (iters == 1 || iters == 2) {
         TileMaps maps;
         if (plan_tile(dtype, in, src, a, maps)) return launch_level_pass_tile(dtype, iters, clamp, a, maps, s);

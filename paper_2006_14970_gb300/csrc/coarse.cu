@@ -31,17 +31,33 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_kernel(const CoarseArgs p)
     const T *A = static_cast<const T *>(p.A);
     const int tid = threadIdx.x;
 
-    // gather I_l and alpha_l of all coarse levels
-    for (int l = 0; l < p.nlev; ++l) {
-        const int w = p.lw[l], h = p.lh[l], n = w * h, o = p.off[l];
-        for (int i = tid; i < n; i += kThreads) {
+    // gather I_l and alpha_l of all coarse levels: every load issued before any store
+    constexpr int kPer = kCoarseTotal / kThreads;
+    float gI[kPer][3], gA[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int idx = tid + k * kThreads;
+        if (idx < p.total) {
+            int l = 0;
+            while (l + 1 < p.nlev && p.off[l + 1] <= idx) ++l;
+            const int w = p.lw[l], h = p.lh[l], i = idx - p.off[l];
             const int x = i % w, y = i / w;
             const int gx = nearest_src(x, p.Iw, w), gy = nearest_src(y, p.Ih, h);
             const T *Ip = I + (long long)gy * p.I_pitch + 3 * gx;
-            Ilv[3 * (o + i) + 0] = ld_elem(Ip + 0);
-            Ilv[3 * (o + i) + 1] = ld_elem(Ip + 1);
-            Ilv[3 * (o + i) + 2] = ld_elem(Ip + 2);
-            Alv[o + i] = ld_elem(A + (long long)gy * p.A_pitch + gx);
+            gI[k][0] = ld_elem(Ip + 0);
+            gI[k][1] = ld_elem(Ip + 1);
+            gI[k][2] = ld_elem(Ip + 2);
+            gA[k] = ld_elem(A + (long long)gy * p.A_pitch + gx);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int idx = tid + k * kThreads;
+        if (idx < p.total) {
+            Ilv[3 * idx + 0] = gI[k][0];
+            Ilv[3 * idx + 1] = gI[k][1];
+            Ilv[3 * idx + 2] = gI[k][2];
+            Alv[idx] = gA[k];
         }
     }
     float2 *cur = bufX, *nxt = bufY;

@@ -108,6 +108,9 @@ size_t level_pass_ring_smem(int slot_bytes);
 cudaError_t launch_level_pass_tile(int dtype, int iters, int clamp, const PassArgs &a,
                                    const TileMaps &m, cudaStream_t s);
 size_t level_pass_tile_smem(int chunk_bytes);
+// Small-level variant: one block per 32 x 16 output tile, all sweeps in shared memory.
+cudaError_t launch_level_small(int dtype, int iters, int clamp, const PassArgs &a,
+                               cudaStream_t s);
 int level_pass_tile_rows();
 // Device error word of the library's bounded waits (0 = no error).
 cudaError_t read_and_clear_device_error(int *code, cudaStream_t s);
