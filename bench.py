@@ -282,7 +282,20 @@ def main():
         roof8 = top_pass_roofline(w8, h8, I8, A8, max(3, args.steps // 2), args.warmup,
                                   "level_pass_7680x4320.md")
         big = {"workload": "single_7680x4320_fp32", "value": world * w8 * h8 / (ms8 * 1e-3) / 1e6,
-               "unit": "Mpix/s", "ms_per_step": ms8, "roofline": roof8}
+               "unit": "Mpix/s", "ms_per_step": ms8, "roofline": roof8, "storage": {}}
+        # reduced-precision storage (I, alpha, F, B in 16 bits; solves in float32): throughput
+        # and the largest difference to the float32 path on the same inputs
+        torch.cuda.synchronize()
+        for name, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+            I16, A16 = I8.to(dt), A8.to(dt)
+            F16, B16 = torch.empty_like(I16), torch.empty_like(I16)
+            ms16 = timed(lambda: fgml.estimate(I16, A16, None, F16, B16), max(3, args.steps // 2),
+                         args.warmup)
+            d = max(float((F16.float() - F8).abs().max()), float((B16.float() - B8).abs().max()))
+            big["storage"][name] = {"value": world * w8 * h8 / (ms16 * 1e-3) / 1e6,
+                                    "unit": "Mpix/s", "ms_per_step": ms16,
+                                    "max_abs_vs_f32_path": d}
+            del I16, A16, F16, B16
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

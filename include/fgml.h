@@ -147,6 +147,31 @@ fg_status fg_estimate_noalloc(const fg_image *I, const fg_image *alpha,
                               const fg_params *params, fg_image *F, fg_image *B,
                               void *stream);
 
+/*
+ * Multi-level foreground estimation of n images of any sizes (Algorithm 1 on each), as
+ * one batch: one launch runs the coarse levels of every image (one block per image),
+ * then one persistent launch runs every remaining level pass of every image from a work
+ * list of (image, level pass, strip) items. An item waits until the pass it reads from
+ * (the previous level or pass of the same image) is complete; the wait is bounded
+ * (2 s) and a timeout is reported by fg_sync() as FG_ERR_TIMEOUT. Results equal those
+ * of fg_estimate on each image within float32 rounding.
+ *  I, alpha, F, B: arrays of n device images (F[i], B[i] the outputs of image i); one
+ *  dtype for the whole batch; outputs must not overlap their own inputs.
+ *  Asynchronous on `stream`; the work list and the per-image levels live in the
+ *  stream's workspace.
+ */
+fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image *alpha,
+                            const fg_params *params, fg_image *F, fg_image *B, void *stream);
+
+/*
+ * Diagnostic of the device-side bounded waits (not part of the method): runs the work-list
+ * kernel on one item that waits for a count nothing ever reaches, with a 20 ms bound, and
+ * checks that the kernel gives up, reports it through the device error word and leaves
+ * the context usable. Returns FG_ERR_TIMEOUT when that happened as intended; any other
+ * status is a failure. Synchronises `stream`.
+ */
+fg_status fg_selftest_bounded_wait(void *stream);
+
 /* Waits for `stream` and reports any device-side error of the library's kernels. */
 fg_status fg_sync(void *stream);
 

@@ -146,6 +146,7 @@ struct Buf {
 struct Workspace {
     Buf lev[2];   // intermediate level states: F then B, each w x h x 3
     Buf stage;    // device staging of the host-memory entry point
+    Buf batch;    // work lists and per-image levels of fg_estimate_batch
     // launch sequences of fg_estimate captured as CUDA graphs, by call signature
     std::map<std::string, cudaGraphExec_t> graphs;
     std::vector<std::string> graph_order;   // oldest first, for eviction
@@ -728,6 +729,7 @@ fg_status fg_release_workspace(void *stream) {
     cudaFree(w.lev[0].p);
     cudaFree(w.lev[1].p);
     cudaFree(w.stage.p);
+    cudaFree(w.batch.p);
     return FG_OK;
 }
 
@@ -871,4 +873,332 @@ extern "C" fg_status fg_estimate_noalloc(const fg_image *I, const fg_image *alph
         if (st != FG_OK) return st;
     }
     return FG_OK;
+}
+
+// ====================================================== work-list batches
+
+namespace {
+
+constexpr int kBatchRingSlotCap = 4096;        // largest ring slot a batch pass may use
+constexpr long long kBatchWaitNs = 2000000000; // bound of one dependency wait (2 s)
+
+// Rows per strip of a batch pass: a few waves of the persistent grid per level.
+int batch_strip_rows(int w, int h) {
+    const int nx = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
+    const long long target = (long long)sm_count() * 4;
+    long long r = ((long long)h * nx + target - 1) / target;
+    return (int)std::min<long long>(std::max<long long>(r, 8), 64);
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+PassArgs batch_pass_args(int dtype, const fg_params &p, const Input &in, const State &src,
+                         void *Fd, void *Bd, long long d_pitch, int w, int h, bool *ring) {
+    PassArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.I = in.I;
+    a.I_pitch = in.I_pitch;
+    a.A = in.A;
+    a.A_pitch = in.A_pitch;
+    a.Iw = in.w;
+    a.Ih = in.h;
+    a.Fs = src.F;
+    a.Bs = src.B;
+    a.s_pitch = src.pitch;
+    a.sw = src.w;
+    a.sh = src.h;
+    a.Fd = Fd;
+    a.Bd = Bd;
+    a.d_pitch = d_pitch;
+    a.w = w;
+    a.h = h;
+    a.eps = p.eps_r;
+    a.omega = p.omega;
+    a.strip_h = batch_strip_rows(w, h);
+    a.n_xstrips = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
+    a.n_warps = a.n_xstrips * ((h + a.strip_h - 1) / a.strip_h);
+    const int es = dtype == kF32 ? 4 : 2;
+    auto r16 = [](int v) { return (v + 15) & ~15; };
+    const int spanI = strip_span(in.w, w), spanS = strip_span(src.w, w);
+    a.capI = r16(3 * spanI * es + 30);
+    a.capA = r16(spanI * es + 30);
+    a.capS = r16(3 * spanS * es + 30);
+    a.slot_bytes = a.capI + a.capA + 2 * a.capS;
+    a.I_end = (const char *)in.I + ((long long)(in.h - 1) * in.I_pitch + 3LL * in.w) * es;
+    a.A_end = (const char *)in.A + ((long long)(in.h - 1) * in.A_pitch + in.w) * es;
+    a.Fs_end = (const char *)src.F + ((long long)(src.h - 1) * src.pitch + 3LL * src.w) * es;
+    a.Bs_end = (const char *)src.B + ((long long)(src.h - 1) * src.pitch + 3LL * src.w) * es;
+    *ring = a.slot_bytes <= kBatchRingSlotCap;
+    if (!*ring) a.capI = a.capA = a.capS = a.slot_bytes = 0;
+    return a;
+}
+
+fg_status batch_launch(int dtype, int clamp, BatchLaunch &b, cudaStream_t s) {
+    int per_sm = 0;
+    cudaError_t e = launch_level_batch(dtype, clamp, b, s, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(e, "batch kernel occupancy");
+    if (per_sm < 1) return fail(FG_ERR_CUDA, "batch kernel does not fit on an SM");
+    b.blocks = std::max(1, std::min(per_sm * sm_count(),
+                                     (b.n_items + level_pass_warps_per_block() - 1) /
+                                         level_pass_warps_per_block()));
+    e = launch_level_batch(dtype, clamp, b, s, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+    return FG_OK;
+}
+
+}  // namespace
+
+extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image *alpha,
+                                       const fg_params *params, fg_image *F, fg_image *B,
+                                       void *stream) {
+    g_err.clear();
+    if (n < 1 || !I || !alpha || !F || !B) return fail(FG_ERR_INVALID_ARG, "empty batch or NULL array");
+    fg_status st;
+    const fg_params p = params_or_default(params);
+    if ((st = check_params(p)) != FG_OK) return st;
+    const fg_dtype dt = I[0].dtype;
+    for (int i = 0; i < n; ++i) {
+        char nm[32];
+        snprintf(nm, sizeof nm, "I[%d]", i);
+        if ((st = check_image(&I[i], 3, nm)) != FG_OK) return st;
+        snprintf(nm, sizeof nm, "alpha[%d]", i);
+        if ((st = check_image(&alpha[i], 1, nm)) != FG_OK) return st;
+        snprintf(nm, sizeof nm, "F[%d]", i);
+        if ((st = check_image(&F[i], 3, nm)) != FG_OK) return st;
+        snprintf(nm, sizeof nm, "B[%d]", i);
+        if ((st = check_image(&B[i], 3, nm)) != FG_OK) return st;
+        if (alpha[i].w != I[i].w || alpha[i].h != I[i].h || F[i].w != I[i].w || F[i].h != I[i].h ||
+            B[i].w != I[i].w || B[i].h != I[i].h)
+            return fail(FG_ERR_INVALID_ARG, "image %d: I, alpha, F and B differ in size", i);
+        if (I[i].dtype != dt || alpha[i].dtype != dt || F[i].dtype != dt || B[i].dtype != dt)
+            return fail(FG_ERR_INVALID_ARG, "image %d: every image of a batch has one dtype", i);
+        if (F[i].row_pitch_bytes != B[i].row_pitch_bytes)
+            return fail(FG_ERR_INVALID_ARG, "image %d: F and B must have the same row pitch", i);
+        if (overlap(&F[i], 3, &B[i], 3) || overlap(&F[i], 3, &I[i], 3) ||
+            overlap(&F[i], 3, &alpha[i], 1) || overlap(&B[i], 3, &I[i], 3) ||
+            overlap(&B[i], 3, &alpha[i], 1))
+            return fail(FG_ERR_INVALID_ARG, "image %d: outputs overlap each other or the inputs", i);
+    }
+    const int dtype = (int)dt, es = elem_size(dt);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    struct Img {
+        Input in;
+        std::vector<Level> lv;
+        int nc;
+        size_t need;
+        size_t buf_off;
+    };
+    std::vector<Img> im(n);
+    bool zero_sweeps = false;
+    size_t buf_total = 0;
+    for (int i = 0; i < n; ++i) {
+        Img &m = im[i];
+        m.in = Input{I[i].ptr, alpha[i].ptr, I[i].row_pitch_bytes / es, alpha[i].row_pitch_bytes / es,
+                     I[i].w, I[i].h};
+        m.lv = plan_levels(m.in.w, m.in.h, p);
+        m.nc = coarse_levels(m.lv);
+        const int nl = (int)m.lv.size();
+        m.need = 0;
+        if (m.nc < nl) m.need = state_bytes(m.lv[m.nc - 1].w, m.lv[m.nc - 1].h, es);
+        for (int l = m.nc; l < nl; ++l) {
+            if (m.lv[l].k == 0) zero_sweeps = true;
+            if (l != nl - 1 || split_sweeps(m.lv[l].k).size() > 1)
+                m.need = std::max(m.need, state_bytes(m.lv[l].w, m.lv[l].h, es));
+        }
+        m.need = align256(m.need);
+        m.buf_off = buf_total;
+        buf_total += 2 * m.need;
+    }
+    if (zero_sweeps) {
+        // levels without sweeps are plain resizes; run such parameter sets image by image
+        for (int i = 0; i < n; ++i)
+            if ((st = estimate(im[i].in, dtype, p, F[i].ptr, B[i].ptr, F[i].row_pitch_bytes / es, s)) != FG_OK)
+                return st;
+        return FG_OK;
+    }
+
+    // pass descriptors in dependency order per image, then items interleaved by rank
+    std::vector<CoarseArgs> coarse(n);
+    std::vector<BatchDesc> descs;
+    std::vector<std::vector<int>> per_image(n);
+    int max_total = 0;
+    // device layout: [coarse args][descs][items][counters][level buffers]; descs need the
+    // buffer addresses, so the blob is sized first and filled after allocation
+    std::vector<std::pair<int, int>> shape;   // (descs count, items count) found by a dry run
+    int ndesc = 0;
+    long long nitems = 0;
+    for (int i = 0; i < n; ++i)
+        for (int l = im[i].nc; l < (int)im[i].lv.size(); ++l)
+            for (int sweeps : split_sweeps(im[i].lv[l].k)) {
+                (void)sweeps;
+                ++ndesc;
+                const int w = im[i].lv[l].w, h = im[i].lv[l].h;
+                const int sh = batch_strip_rows(w, h);
+                nitems += (long long)((w + level_pass_strip_width() - 1) / level_pass_strip_width()) *
+                          ((h + sh - 1) / sh);
+            }
+    if (nitems > (1LL << 30)) return fail(FG_ERR_INVALID_ARG, "batch too large");
+    const size_t off_coarse = 0;
+    const size_t off_desc = align256(off_coarse + n * sizeof(CoarseArgs));
+    const size_t off_items = align256(off_desc + ndesc * sizeof(BatchDesc));
+    const size_t off_cnt = align256(off_items + nitems * sizeof(BatchItem));
+    const size_t off_bufs = align256(off_cnt + (1 + ndesc) * sizeof(int));
+    Workspace &ws = workspace_for(s);
+    if ((st = ensure(ws.batch, off_bufs + buf_total + 256, s)) != FG_OK) return st;
+    char *dev = (char *)ws.batch.p;
+
+    int slot_max = 16;
+    for (int i = 0; i < n; ++i) {
+        Img &m = im[i];
+        const int nl = (int)m.lv.size();
+        Buf b0{dev + off_bufs + m.buf_off, m.need}, b1{dev + off_bufs + m.buf_off + m.need, m.need};
+        const Buf *bufs[2] = {&b0, &b1};
+        CoarseArgs &ca = coarse[i];
+        std::memset(&ca, 0, sizeof ca);
+        ca.I = m.in.I;
+        ca.I_pitch = m.in.I_pitch;
+        ca.A = m.in.A;
+        ca.A_pitch = m.in.A_pitch;
+        ca.Iw = m.in.w;
+        ca.Ih = m.in.h;
+        ca.nlev = m.nc;
+        for (int l = 0; l < m.nc; ++l) {
+            ca.lw[l] = m.lv[l].w;
+            ca.lh[l] = m.lv[l].h;
+            ca.lk[l] = m.lv[l].k;
+            ca.off[l] = ca.total;
+            ca.total += m.lv[l].w * m.lv[l].h;
+        }
+        ca.eps = p.eps_r;
+        ca.omega = p.omega;
+        ca.init = p.init;
+        max_total = std::max(max_total, ca.total);
+        State src{};
+        int buf = -1;
+        if (m.nc == nl) {
+            ca.Fd = F[i].ptr;
+            ca.Bd = B[i].ptr;
+            ca.d_pitch = F[i].row_pitch_bytes / es;
+        } else {
+            src = state_in(b0, m.lv[m.nc - 1].w, m.lv[m.nc - 1].h, es);
+            buf = 0;
+            ca.Fd = (void *)src.F;
+            ca.Bd = (void *)src.B;
+            ca.d_pitch = src.pitch;
+        }
+        int prev = -1;
+        for (int l = m.nc; l < nl; ++l) {
+            const std::vector<int> passes = split_sweeps(m.lv[l].k);
+            for (size_t j = 0; j < passes.size(); ++j) {
+                const bool to_caller = l == nl - 1 && j + 1 == passes.size();
+                const int w = m.lv[l].w, h = m.lv[l].h;
+                void *Fd, *Bd;
+                long long dp;
+                State dst{};
+                int nb = buf;
+                if (to_caller) {
+                    Fd = F[i].ptr;
+                    Bd = B[i].ptr;
+                    dp = F[i].row_pitch_bytes / es;
+                } else {
+                    nb = buf == 0 ? 1 : 0;
+                    dst = state_in(*bufs[nb], w, h, es);
+                    Fd = (void *)dst.F;
+                    Bd = (void *)dst.B;
+                    dp = dst.pitch;
+                }
+                BatchDesc d;
+                std::memset(&d, 0, sizeof d);
+                bool ring = false;
+                d.a = batch_pass_args(dtype, p, m.in, src, Fd, Bd, dp, w, h, &ring);
+                d.iters = passes[j];
+                d.dep = prev;
+                d.dep_count = prev >= 0 ? descs[prev].a.n_warps : 0;
+                d.ring = ring ? 1 : 0;
+                if (ring) slot_max = std::max(slot_max, d.a.slot_bytes);
+                prev = (int)descs.size();
+                per_image[i].push_back(prev);
+                descs.push_back(d);
+                if (!to_caller) {
+                    src = dst;
+                    buf = nb;
+                }
+            }
+        }
+    }
+    // every ring pass uses the batch's largest slot layout
+    std::vector<BatchItem> items;
+    items.reserve((size_t)nitems);
+    for (size_t rank = 0;; ++rank) {
+        bool any = false;
+        for (int i = 0; i < n; ++i) {
+            if (rank >= per_image[i].size()) continue;
+            any = true;
+            const int dix = per_image[i][rank];
+            for (int wi = 0; wi < descs[dix].a.n_warps; ++wi) items.push_back(BatchItem{dix, wi});
+        }
+        if (!any) break;
+    }
+    for (BatchDesc &d : descs)
+        if (d.ring) {
+            d.a.slot_bytes = slot_max;
+        }
+
+    std::vector<char> blob(off_bufs, 0);
+    std::memcpy(blob.data() + off_coarse, coarse.data(), n * sizeof(CoarseArgs));
+    if (!descs.empty()) std::memcpy(blob.data() + off_desc, descs.data(), descs.size() * sizeof(BatchDesc));
+    if (!items.empty()) std::memcpy(blob.data() + off_items, items.data(), items.size() * sizeof(BatchItem));
+    cudaError_t e = cudaMemcpyAsync(dev, blob.data(), blob.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of the batch work list");
+    e = launch_coarse_batch(dtype, p.clamp, reinterpret_cast<const CoarseArgs *>(dev + off_coarse), n,
+                            max_total, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched coarse kernel launch");
+    if (items.empty()) return FG_OK;
+    BatchLaunch b;
+    b.descs = reinterpret_cast<const BatchDesc *>(dev + off_desc);
+    b.items = reinterpret_cast<const BatchItem *>(dev + off_items);
+    b.n_items = (int)items.size();
+    b.counters = reinterpret_cast<int *>(dev + off_cnt);
+    b.wait_ns = kBatchWaitNs;
+    b.slot_bytes = slot_max;
+    return batch_launch(dtype, p.clamp, b, s);
+}
+
+extern "C" fg_status fg_selftest_bounded_wait(void *stream) {
+    g_err.clear();
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace &ws = workspace_for(s);
+    fg_status st = ensure(ws.batch, 4096, s);
+    if (st != FG_OK) return st;
+    // one item that waits for its own pass: the count it waits for is never reached
+    BatchDesc d;
+    std::memset(&d, 0, sizeof d);
+    d.iters = 2;
+    d.dep = 0;
+    d.dep_count = 1;
+    BatchItem it{0, 0};
+    char *dev = (char *)ws.batch.p;
+    std::vector<char> blob(1024, 0);
+    std::memcpy(blob.data(), &d, sizeof d);
+    std::memcpy(blob.data() + 512, &it, sizeof it);
+    cudaError_t e = cudaMemcpyAsync(dev, blob.data(), blob.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test upload");
+    BatchLaunch b;
+    b.descs = reinterpret_cast<const BatchDesc *>(dev);
+    b.items = reinterpret_cast<const BatchItem *>(dev + 512);
+    b.n_items = 1;
+    b.counters = reinterpret_cast<int *>(dev + 768);
+    b.wait_ns = 20000000;   // 20 ms
+    b.slot_bytes = 16;
+    b.blocks = 1;
+    e = launch_level_batch(kF32, 1, b, s, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test synchronize");
+    int code = 0;
+    e = read_and_clear_device_error(&code, s);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test error word");
+    if (code != 2) return fail(FG_ERR_CUDA, "the bounded wait did not report a timeout (code %d)", code);
+    return fail(FG_ERR_TIMEOUT, "bounded wait gave up as intended");
 }

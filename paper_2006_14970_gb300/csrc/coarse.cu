@@ -19,7 +19,21 @@ constexpr int kThreads = 1024;
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 
 template <typename T, bool CLAMP>
+__device__ __forceinline__ void coarse_body(const CoarseArgs &p);
+
+template <typename T, bool CLAMP>
 __global__ void __launch_bounds__(kThreads, 1) coarse_kernel(const CoarseArgs p) {
+    coarse_body<T, CLAMP>(p);
+}
+
+// One block per image of a batch; each reads its arguments from the device list.
+template <typename T, bool CLAMP>
+__global__ void __launch_bounds__(kThreads, 1) coarse_batch_kernel(const CoarseArgs *list) {
+    coarse_body<T, CLAMP>(list[blockIdx.x]);
+}
+
+template <typename T, bool CLAMP>
+__device__ __forceinline__ void coarse_body(const CoarseArgs &p) {
     extern __shared__ __align__(16) float sm[];
     // [0, 3 * kCoarseCap) float2: buffer X; then buffer Y; then per level I (3 floats per
     // pixel) and alpha, at the offsets p.off[l] (in pixels)
@@ -153,7 +167,30 @@ cudaError_t launch_t(const CoarseArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <typename T, bool CLAMP>
+cudaError_t launch_batch_t(const CoarseArgs *list, int n, int max_total, cudaStream_t s) {
+    const size_t smem = coarse_smem_bytes(max_total);
+    cudaError_t e = cudaFuncSetAttribute(coarse_batch_kernel<T, CLAMP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    coarse_batch_kernel<T, CLAMP><<<n, kThreads, smem, s>>>(list);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_coarse_batch(int dtype, int clamp, const CoarseArgs *list, int n,
+                                int max_total, cudaStream_t s) {
+    if (n < 1 || max_total > kCoarseTotal) return cudaErrorInvalidValue;
+    switch (dtype) {
+        case kF32: return clamp ? launch_batch_t<float, true>(list, n, max_total, s) : launch_batch_t<float, false>(list, n, max_total, s);
+        case kBF16:
+            return clamp ? launch_batch_t<__nv_bfloat16, true>(list, n, max_total, s)
+                         : launch_batch_t<__nv_bfloat16, false>(list, n, max_total, s);
+        case kF16: return clamp ? launch_batch_t<__half, true>(list, n, max_total, s) : launch_batch_t<__half, false>(list, n, max_total, s);
+    }
+    return cudaErrorInvalidValue;
+}
 
 size_t coarse_smem_bytes(int total_pixels) {
     return 2 * 3 * kCoarseCap * sizeof(float2) + (size_t)total_pixels * 4 * sizeof(float);

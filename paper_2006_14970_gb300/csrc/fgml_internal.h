@@ -62,6 +62,34 @@ struct PassArgs {
     int tile_offA, tile_offF, tile_offB, tile_chunk, tile_tx;
 };
 
+// One level pass of a work-list batch.
+struct BatchDesc {
+    PassArgs a;
+    int iters;       // sweeps of this pass (1 or 2)
+    int dep;         // pass whose strips must all be done first (-1: none)
+    int dep_count;   // strips of that pass
+    int ring;        // 1: rows through the TMA ring (a.cap*/slot_bytes set), 0: plain loads
+};
+
+// One work item: strip `warp` of pass `desc`.
+struct BatchItem {
+    int desc, warp;
+};
+
+struct BatchLaunch {
+    const BatchDesc *descs;
+    const BatchItem *items;
+    int n_items;
+    int *counters;       // [0]: next item to pop, [1 + d]: finished strips of pass d
+    long long wait_ns;   // bound of one dependency wait
+    int slot_bytes;      // ring slot size (largest over the ring passes, >= 16)
+    int blocks;          // persistent grid (at most the resident blocks)
+};
+
+// Launches the batch kernel, or (blocks_per_sm != NULL) only reports its occupancy.
+cudaError_t launch_level_batch(int dtype, int clamp, const BatchLaunch &b, cudaStream_t s,
+                               int *blocks_per_sm);
+
 // Tensor maps of the tile variant: I, alpha, and the starting F and B, as 2D tensors of
 // elements (row length = channels x width).
 struct TileMaps {
@@ -115,6 +143,9 @@ int level_pass_tile_rows();
 // Device error word of the library's bounded waits (0 = no error).
 cudaError_t read_and_clear_device_error(int *code, cudaStream_t s);
 cudaError_t launch_coarse(int dtype, int clamp, const CoarseArgs &a, cudaStream_t s);
+// Coarse levels of many images, one block per image (list: device array of n args).
+cudaError_t launch_coarse_batch(int dtype, int clamp, const CoarseArgs *list, int n,
+                                int max_total, cudaStream_t s);
 size_t coarse_smem_bytes(int total_pixels);
 
 }  // namespace fgml

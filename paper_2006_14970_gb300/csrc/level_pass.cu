@@ -207,8 +207,20 @@ struct Ctl {
 
 // ------------------------------------------------------------------ row sources
 
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+
+// Loads of F and B written earlier in the same launch (work-list batches) bypass the
+// per-SM caches; everything else goes through the read-only path.
+template <typename T, bool COHERENT>
+__device__ __forceinline__ float ld_state(const T *p) {
+    if (COHERENT) return to_f(__ldcg(p));
+    return ld_elem(p);
+}
+
 // Register variant: plain loads of row r+1 issued while row r is processed.
-template <typename T>
+template <typename T, bool COHERENT = false>
 struct RegSource {
     Raw nxt;
 
@@ -225,10 +237,10 @@ struct RegSource {
         for (int c = 0; c < 3; ++c) {
             o.i0[c] = ld_elem(Ir + 3 * g.gi0 + c);
             o.i1[c] = ld_elem(Ir + 3 * g.gi1 + c);
-            o.f0[c] = ld_elem(Fr + 3 * g.gs0 + c);
-            o.f1[c] = ld_elem(Fr + 3 * g.gs1 + c);
-            o.b0[c] = ld_elem(Br + 3 * g.gs0 + c);
-            o.b1[c] = ld_elem(Br + 3 * g.gs1 + c);
+            o.f0[c] = ld_state<T, COHERENT>(Fr + 3 * g.gs0 + c);
+            o.f1[c] = ld_state<T, COHERENT>(Fr + 3 * g.gs1 + c);
+            o.b0[c] = ld_state<T, COHERENT>(Br + 3 * g.gs0 + c);
+            o.b1[c] = ld_state<T, COHERENT>(Br + 3 * g.gs1 + c);
         }
     }
     __device__ __forceinline__ void start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
@@ -247,9 +259,6 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
 // floor((2r + 1) S / (2D)) for r = r0, r0 + 1, ... without a division per row.
 struct RowMap {
@@ -340,7 +349,7 @@ struct RingSource {
                 const uint32_t dst = slot_s + seg_off(p, k) + ((uint32_t)reinterpret_cast<uintptr_t>(a) & 15u);
                 const T *src = reinterpret_cast<const T *>(a);
                 for (int e = lane; e < seg_len(k) / (int)sizeof(T); e += 32) {
-                    T v = src[e];
+                    T v = __ldcg(src + e);
                     unsigned short u;
                     if (sizeof(T) == 4) {
                         asm volatile("st.shared.b32 [%0], %1;" :: "r"(dst + 4u * e), "r"(__float_as_uint(*reinterpret_cast<float *>(&v))) : "memory");
@@ -388,6 +397,29 @@ struct RingSource {
                 : "=r"(ok) : "r"(bar), "r"(par), "r"(kWaitHintNs) : "memory");
         }
         return __all_sync(kFull, ok != 0);
+    }
+
+    // The strip's source column ranges: lanes load columns [xf, xl] of the level.
+    __device__ __forceinline__ void setup(const PassArgs &p, const LaneGeo &g, int ln) {
+        const int X0 = g.x - 2 * ln;
+        const int xf = min(max(X0, 0), p.w - 1);
+        const int xl = min(max(X0 + kLaneCols - 1, 0), p.w - 1);
+        const int giF = nearest_src(xf, p.Iw, p.w);
+        const int nI = nearest_src(xl, p.Iw, p.w) - giF + 1;
+        const int gsF = nearest_src(xf, p.sw, p.w);
+        const int nS = nearest_src(xl, p.sw, p.w) - gsF + 1;
+        const int es = (int)sizeof(T);
+        colI = 3 * giF * es;
+        colA = giF * es;
+        colS = 3 * gsF * es;
+        lenI = 3 * nI * es;
+        lenA = nI * es;
+        lenS = 3 * nS * es;
+        li = 3 * (g.gi0 - giF);
+        la = g.gi0 - giF;
+        ls = 3 * (g.gs0 - gsF);
+        dI = g.gi1 - g.gi0;
+        dS = g.gs1 - g.gs0;
     }
 
     __device__ __forceinline__ void start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
@@ -534,7 +566,7 @@ __device__ __forceinline__ void lane_setup(const PassArgs &p, int warp, int lane
 }
 
 template <typename T, int K, bool CLAMP, typename Src>
-__device__ __forceinline__ void run_strip(const PassArgs &p, const LaneGeo &g, const Ctl &ct,
+__device__ __forceinline__ bool run_strip(const PassArgs &p, const LaneGeo &g, const Ctl &ct,
                                           const Out &out, Src &src) {
     RowK S0, S1, S2;
     FB Q0, Q1, Q2, P0, P1, P2;
@@ -555,6 +587,7 @@ __device__ __forceinline__ void run_strip(const PassArgs &p, const LaneGeo &g, c
         if ((threadIdx.x & 31) == 0) atomicExch(&g_device_error, 1);
         src.abort();
     }
+    return ok;
 }
 
 template <typename T, int K, bool CLAMP>
@@ -592,26 +625,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kRingMinBlocks) level_pas
     src.fslot = src.gslot = 0;
     src.fpar = src.gpar = 0;
     src.issued = src.parity = 0;
-    // the warp's source column ranges: lanes load columns [xf, xl] of the level
-    const int X0 = g.x - 2 * lane;
-    const int xf = min(max(X0, 0), p.w - 1);
-    const int xl = min(max(X0 + kLaneCols - 1, 0), p.w - 1);
-    const int giF = nearest_src(xf, p.Iw, p.w);
-    const int nI = nearest_src(xl, p.Iw, p.w) - giF + 1;
-    const int gsF = nearest_src(xf, p.sw, p.w);
-    const int nS = nearest_src(xl, p.sw, p.w) - gsF + 1;
-    const int es = (int)sizeof(T);
-    src.colI = 3 * giF * es;
-    src.colA = giF * es;
-    src.colS = 3 * gsF * es;
-    src.lenI = 3 * nI * es;
-    src.lenA = nI * es;
-    src.lenS = 3 * nS * es;
-    src.li = 3 * (g.gi0 - giF);
-    src.la = g.gi0 - giF;
-    src.ls = 3 * (g.gs0 - gsF);
-    src.dI = g.gi1 - g.gi0;
-    src.dS = g.gs1 - g.gs0;
+    src.setup(p, g, lane);
     if (lane == 0) {
         for (int s = 0; s < kRingSlots; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(src.bar0 + 8u * s) : "memory");
@@ -798,6 +812,116 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_tile_kernel
     run_strip<T, K, CLAMP>(p, g, ct, out, src);
 }
 
+// Work-list batch: one persistent launch runs the level passes of many images. Each
+// warp pops (level pass, strip) items in list order; an item first waits (bounded, with
+// backoff) until every strip of the pass it depends on has finished, then runs like a
+// strip of the ring or register variant, then counts itself done. The list holds every
+// pass after the passes it depends on, and the grid is no larger than what is resident,
+// so the items an item waits for are always running or finished. The ring's slot and
+// phase counters carry over from item to item, so its mbarriers are initialised once.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool wait_count(const int *c, int need, long long budget_ns) {
+    const unsigned long long t0 = global_ns();
+    unsigned ns = 32;
+    for (int i = 0; i < (1 << 26); ++i) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+        if (v >= need) return true;
+        if ((long long)(global_ns() - t0) > budget_ns) return false;
+        __nanosleep(ns);
+        if (ns < 1024) ns *= 2;
+    }
+    return false;
+}
+
+template <typename T, bool CLAMP>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_batch_kernel(
+    const BatchDesc *descs, const BatchItem *items, int n_items, int *counters,
+    long long wait_ns, int slot_bytes) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ PassArgs sp[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+
+    RingSource<T> ring;
+    ring.sm = smem;
+    ring.sbase = smem_addr(smem);
+    ring.lane = lane;
+    ring.slots_s = smem_addr(smem) + (uint32_t)(wib * kRingSlots * slot_bytes);
+    ring.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * kRingSlots * slot_bytes) +
+                8u * (uint32_t)(wib * kRingSlots);
+    ring.fslot = ring.gslot = 0;
+    ring.fpar = ring.gpar = 0;
+    ring.issued = ring.parity = 0;
+    if (lane == 0) {
+        for (int s = 0; s < kRingSlots; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(ring.bar0 + 8u * s) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(&counters[0], 1);
+        idx = __shfl_sync(kFull, idx, 0);
+        if (idx >= n_items) break;
+        const BatchItem it = items[idx];
+        const BatchDesc &d = descs[it.desc];
+        const int *src_words = reinterpret_cast<const int *>(&d.a);
+        int *dst_words = reinterpret_cast<int *>(&sp[wib]);
+        for (int k = lane; k < (int)(sizeof(PassArgs) / sizeof(int)); k += 32) dst_words[k] = src_words[k];
+        const int iters = d.iters, dep = d.dep, dep_count = d.dep_count, use_ring = d.ring;
+        __syncwarp();
+        const PassArgs &p = sp[wib];
+        if (dep >= 0) {
+            int ok = 1;
+            if (lane == 0) ok = wait_count(&counters[1 + dep], dep_count, wait_ns) ? 1 : 0;
+            ok = __shfl_sync(kFull, ok, 0);
+            if (!ok) {
+                if (lane == 0) atomicExch(&g_device_error, 2);
+                break;
+            }
+            __threadfence();
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
+        LaneGeo g;
+        Ctl ct;
+        Out out;
+        bool ok;
+        if (use_ring) {
+            if (iters == 1) {
+                lane_setup<T>(p, it.warp, lane, g, ct, out, 1);
+                ring.setup(p, g, lane);
+                ok = run_strip<T, 1, CLAMP>(p, g, ct, out, ring);
+            } else {
+                lane_setup<T>(p, it.warp, lane, g, ct, out, 2);
+                ring.setup(p, g, lane);
+                ok = run_strip<T, 2, CLAMP>(p, g, ct, out, ring);
+            }
+        } else {
+            RegSource<T, true> reg;
+            if (iters == 1) {
+                lane_setup<T>(p, it.warp, lane, g, ct, out, 1);
+                ok = run_strip<T, 1, CLAMP>(p, g, ct, out, reg);
+            } else {
+                lane_setup<T>(p, it.warp, lane, g, ct, out, 2);
+                ok = run_strip<T, 2, CLAMP>(p, g, ct, out, reg);
+            }
+        }
+        if (!ok) break;
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            atomicAdd(&counters[1 + it.desc], 1);
+        }
+    }
+}
+
 // Zero sweeps: the level's F and B are the nearest resize of the starting state.
 template <typename T>
 __global__ void resize_fb_kernel(const PassArgs p) {
@@ -915,6 +1039,33 @@ size_t level_pass_tile_smem(int chunk_bytes) {
 }
 
 int level_pass_tile_rows() { return kTileRows; }
+
+template <typename T, bool CLAMP>
+cudaError_t batch_t(const BatchLaunch &b, cudaStream_t s, int *blocks_per_sm) {
+    const size_t smem = level_pass_ring_smem(b.slot_bytes);
+    cudaError_t e = cudaFuncSetAttribute(level_batch_kernel<T, CLAMP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, level_batch_kernel<T, CLAMP>,
+                                                             kWarpsPerBlock * 32, smem);
+    }
+    level_batch_kernel<T, CLAMP><<<b.blocks, kWarpsPerBlock * 32, smem, s>>>(
+        b.descs, b.items, b.n_items, b.counters, b.wait_ns, b.slot_bytes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_batch(int dtype, int clamp, const BatchLaunch &b, cudaStream_t s,
+                               int *blocks_per_sm) {
+    switch (dtype) {
+        case kF32: return clamp ? batch_t<float, true>(b, s, blocks_per_sm) : batch_t<float, false>(b, s, blocks_per_sm);
+        case kBF16:
+            return clamp ? batch_t<__nv_bfloat16, true>(b, s, blocks_per_sm)
+                         : batch_t<__nv_bfloat16, false>(b, s, blocks_per_sm);
+        case kF16: return clamp ? batch_t<__half, true>(b, s, blocks_per_sm) : batch_t<__half, false>(b, s, blocks_per_sm);
+    }
+    return cudaErrorInvalidValue;
+}
 
 size_t level_pass_ring_smem(int slot_bytes) {
     return (size_t)kWarpsPerBlock * kRingSlots * (size_t)slot_bytes +

@@ -73,6 +73,11 @@ def load():
     lib.fg_level_pass.argtypes = [P(Image), P(Image), P(Image), P(Image), ctypes.c_int,
                                   P(Params), P(Image), P(Image), vp]
     lib.fg_level_pass.restype = ctypes.c_int
+    lib.fg_estimate_batch.argtypes = [ctypes.c_int, P(Image), P(Image), P(Params), P(Image),
+                                      P(Image), vp]
+    lib.fg_estimate_batch.restype = ctypes.c_int
+    lib.fg_selftest_bounded_wait.argtypes = [vp]
+    lib.fg_selftest_bounded_wait.restype = ctypes.c_int
     lib.fg_sync.argtypes = [vp]
     lib.fg_sync.restype = ctypes.c_int
     lib.fg_release_workspace.argtypes = [vp]
@@ -190,6 +195,30 @@ def level_pass(I, alpha, F_src, B_src, iters: int, w: int, h: int, p: Params | N
                                 ctypes.byref(p) if p is not None else None,
                                 ctypes.byref(imgs[4]), ctypes.byref(imgs[5]), _stream(stream)))
     return F_dst, B_dst
+
+
+def estimate_batch(images, p: Params | None = None, outputs=None, stream=None):
+    """fg_estimate_batch on a list of (I, alpha) device tensor pairs; returns [(F, B)]."""
+    n = len(images)
+    if n == 0:
+        return []
+    if outputs is None:
+        outputs = [(torch.empty_like(I, memory_format=torch.contiguous_format),
+                    torch.empty_like(I, memory_format=torch.contiguous_format))
+                   for I, _ in images]
+    arr = Image * n
+    iI = arr(*[_image(I, 3, "I") for I, _ in images])
+    iA = arr(*[_image(A, 1, "alpha") for _, A in images])
+    iF = arr(*[_image(F, 3, "F") for F, _ in outputs])
+    iB = arr(*[_image(B, 3, "B") for _, B in outputs])
+    _check(load().fg_estimate_batch(n, iI, iA, ctypes.byref(p) if p is not None else None,
+                                    iF, iB, _stream(stream)))
+    return outputs
+
+
+def selftest_bounded_wait(stream=None) -> int:
+    """Runs the bounded-wait diagnostic; returns its status (FG_ERR_TIMEOUT = as intended)."""
+    return load().fg_selftest_bounded_wait(_stream(stream))
 
 
 def sync(stream=None):

@@ -1,0 +1,109 @@
+"""Work-list batches: many images of uneven sizes in one coarse launch plus one persistent
+launch. Every image must match its single-image result and the FP64 oracle within the
+parity tolerance; the bounded dependency wait must give up cleanly when its count is
+never reached."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2006_14970_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def _dev(a, dt=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda().to(dt)
+
+
+def _samples(sizes, seed):
+    return [synth.make_sample(w, h, seed + i) for i, (w, h) in enumerate(sizes)]
+
+
+def test_batch_uneven_sizes_matches_single_and_oracle(fgml):
+    sizes = [(1, 1), (5, 3), (40, 33), (64, 64), (77, 301), (300, 200), (517, 389), (1000, 97),
+             (33, 1024), (1939, 611)]
+    ss = _samples(sizes, 500)
+    imgs = [(_dev(s.I), _dev(s.alpha)) for s in ss]
+    out = fgml.estimate_batch(imgs)
+    fgml.sync()
+    for (I, A), (F, B), s in zip(imgs, out, ss):
+        Fs, Bs = fgml.estimate(I, A)
+        torch.cuda.synchronize()
+        assert float((F - Fs).abs().max()) <= TOL and float((B - Bs).abs().max()) <= TOL
+        Fo, Bo = oracle.ml(s.I, s.alpha)
+        assert np.abs(F.cpu().numpy() - Fo).max() <= TOL
+        assert np.abs(B.cpu().numpy() - Bo).max() <= TOL
+
+
+def test_batch_repeated_and_reordered(fgml):
+    sizes = [(256, 300), (640, 480), (128, 1024)]
+    ss = _samples(sizes, 600)
+    imgs = [(_dev(s.I), _dev(s.alpha)) for s in ss]
+    a = fgml.estimate_batch(imgs)
+    b = fgml.estimate_batch(imgs[::-1])[::-1]
+    c = fgml.estimate_batch(imgs)
+    fgml.sync()
+    for x, y, z in zip(a, b, c):
+        assert torch.equal(x[0], z[0]) and torch.equal(x[1], z[1])
+        assert float((x[0] - y[0]).abs().max()) <= TOL and float((x[1] - y[1]).abs().max()) <= TOL
+
+
+@pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
+def test_batch_reduced_precision_within_bound(fgml, dt):
+    # each level's F and B are rounded to the storage type, so the batch and the
+    # single-image kernels may differ by a few units of the last place; both must stay
+    # within the stated reduced-precision bound of the oracle on the rounded inputs
+    bound = {torch.bfloat16: 1.2e-2, torch.float16: 1.5e-3}[dt]
+    ss = _samples([(300, 211), (1024, 768), (70, 900)], 700)
+    imgs = [(_dev(s.I, dt), _dev(s.alpha, dt)) for s in ss]
+    out = fgml.estimate_batch(imgs)
+    fgml.sync()
+    for (I, A), (F, B) in zip(imgs, out):
+        Fo, Bo = oracle.ml(I.float().cpu().numpy(), A.float().cpu().numpy())
+        assert np.abs(F.float().cpu().numpy() - Fo).max() <= bound
+        assert np.abs(B.float().cpu().numpy() - Bo).max() <= bound
+
+
+def test_batch_parameters(fgml):
+    ss = _samples([(181, 97), (400, 257)], 800)
+    imgs = [(_dev(s.I), _dev(s.alpha)) for s in ss]
+    for kw in [dict(clamp=0), dict(small_iters=3, big_iters=5), dict(big_iters=0),
+               dict(eps_r=0.02, omega=1.0)]:
+        p = fgml.params(**kw)
+        out = fgml.estimate_batch(imgs, p)
+        fgml.sync()
+        for (I, A), (F, B) in zip(imgs, out):
+            Fs, Bs = fgml.estimate(I, A, p)
+            torch.cuda.synchronize()
+            tol = TOL if kw.get("clamp", 1) else 5e-4
+            assert float((F - Fs).abs().max()) <= tol and float((B - Bs).abs().max()) <= tol, kw
+
+
+def test_batch_of_64_uneven_images(fgml):
+    # the batched workload: 64 images, sides log-uniform in [256, 2048]
+    ss = synth.batch(64)
+    imgs = [(_dev(s.I), _dev(s.alpha)) for s in ss]
+    out = fgml.estimate_batch(imgs)
+    fgml.sync()
+    for k, ((I, A), (F, B)) in enumerate(zip(imgs, out)):
+        Fs, Bs = fgml.estimate(I, A)
+        torch.cuda.synchronize()
+        assert float((F - Fs).abs().max()) <= TOL and float((B - Bs).abs().max()) <= TOL, k
+    for k in (0, 17, 42):
+        Fo, Bo = oracle.ml(ss[k].I, ss[k].alpha)
+        assert np.abs(out[k][0].cpu().numpy() - Fo).max() <= TOL
+        assert np.abs(out[k][1].cpu().numpy() - Bo).max() <= TOL
+
+
+def test_bounded_wait_gives_up_and_context_survives(fgml):
+    st = fgml.selftest_bounded_wait()
+    assert st == fgml.FG_ERR_TIMEOUT, fgml.load().fg_last_error()
+    # the device is still usable and the error word is clear again
+    s = synth.make_sample(200, 150, 900)
+    F, B = fgml.estimate(_dev(s.I), _dev(s.alpha))
+    fgml.sync()
+    Fo, Bo = oracle.ml(s.I, s.alpha)
+    assert np.abs(F.cpu().numpy() - Fo).max() <= TOL
