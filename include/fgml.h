@@ -172,6 +172,65 @@ fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image *alpha,
  */
 fg_status fg_selftest_bounded_wait(void *stream);
 
+/* ------------------------------------------------------------------ serving
+ * A server runs jobs submitted at any time with continuous batching on the current
+ * device: a scheduler thread admits queued jobs in arrival order while a slot is free and
+ * the job's device bytes fit in the HBM budget, copies their inputs up, merges every
+ * admitted job not yet launched (of one dtype) into one fg_estimate_batch launch on an
+ * idle compute stream, and completes jobs as their batch finishes (outputs copied back
+ * to the job's host buffers). Jobs arriving while batches run join the next batch as
+ * slots and memory free up, and that batch overlaps the running ones on the device. The
+ * paper has no serving layer; the method run for each job is Algorithm 1.
+ */
+typedef struct fg_server fg_server;
+
+typedef struct {
+    int max_inflight_jobs;       /* admitted and unfinished jobs at most (default 256) */
+    long long hbm_budget_bytes;  /* device bytes jobs may hold (<= 0: half the free memory) */
+    int streams;                 /* batches in flight at most, 1..16 (default 2) */
+    int max_batch;               /* jobs per batch at most (default 64) */
+    fg_params params;            /* method parameters for every job */
+} fg_server_cfg;
+
+typedef struct {
+    const void *I;       /* HOST w x h x 3, packed, element type dtype */
+    const void *alpha;   /* HOST w x h, packed */
+    int w, h;
+    fg_dtype dtype;
+    void *F, *B;         /* HOST w x h x 3 outputs, written when the job is done */
+} fg_request;
+
+typedef struct {
+    long long submitted, completed, failed, batches;
+    long long pixels;        /* full-resolution pixels of completed jobs */
+    long long max_inflight;  /* most jobs admitted at once */
+    long long max_bytes;     /* most device bytes held by jobs at once */
+    long long budget_bytes;  /* the HBM budget in force */
+} fg_server_stats;
+
+/* Fills *c with defaults. */
+void fg_server_cfg_default(fg_server_cfg *c);
+/* Creates a server (NULL cfg: defaults) bound to the current device. */
+fg_status fg_server_create(const fg_server_cfg *cfg, fg_server **out);
+/* Queues a job; the host buffers must stay valid until the job is done. A job larger
+ * than the whole budget is rejected with FG_ERR_INVALID_ARG. Thread-safe. */
+fg_status fg_server_submit(fg_server *s, const fg_request *r, uint64_t *ticket);
+/* *done = 1 once the job's outputs are in its host buffers; a failed job returns its
+ * error status. */
+fg_status fg_server_poll(fg_server *s, uint64_t ticket, int *done);
+/* Blocks until the job is done (timeout_ms < 0: no limit); FG_ERR_TIMEOUT on timeout. */
+fg_status fg_server_wait(fg_server *s, uint64_t ticket, int timeout_ms);
+/* Submit and completion times of a finished job, seconds since the server started. */
+fg_status fg_server_times(fg_server *s, uint64_t ticket, double *submit_s, double *done_s);
+/* Forgets a finished job's record. */
+fg_status fg_server_release(fg_server *s, uint64_t ticket);
+/* Counters since creation. */
+fg_status fg_server_get_stats(fg_server *s, fg_server_stats *out);
+/* Finishes every queued and running job, then frees the server. */
+void fg_server_destroy(fg_server *s);
+/* Message of the calling thread's last server error. */
+const char *fg_server_last_error(void);
+
 /* Waits for `stream` and reports any device-side error of the library's kernels. */
 fg_status fg_sync(void *stream);
 

@@ -253,3 +253,130 @@ def estimate_noalloc(I: torch.Tensor, alpha: torch.Tensor, p: Params | None = No
     _check(fn(ctypes.byref(iI), ctypes.byref(iA), ctypes.byref(p) if p is not None else None,
               ctypes.byref(iF), ctypes.byref(iB), _stream(stream)))
     return F, B
+
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("max_inflight_jobs", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_longlong),
+                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int), ("params", Params)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_void_p), ("alpha", ctypes.c_void_p), ("w", ctypes.c_int),
+                ("h", ctypes.c_int), ("dtype", ctypes.c_int), ("F", ctypes.c_void_p),
+                ("B", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_longlong) for n in
+                ("submitted", "completed", "failed", "batches", "pixels", "max_inflight",
+                 "max_bytes", "budget_bytes")]
+
+
+def _server_lib():
+    lib = load()
+    if not getattr(lib, "_server_bound", False):
+        P = ctypes.POINTER
+        vp = ctypes.c_void_p
+        lib.fg_server_cfg_default.argtypes = [P(ServerCfg)]
+        lib.fg_server_cfg_default.restype = None
+        lib.fg_server_create.argtypes = [P(ServerCfg), P(vp)]
+        lib.fg_server_create.restype = ctypes.c_int
+        lib.fg_server_submit.argtypes = [vp, P(Request), P(ctypes.c_uint64)]
+        lib.fg_server_submit.restype = ctypes.c_int
+        lib.fg_server_poll.argtypes = [vp, ctypes.c_uint64, P(ctypes.c_int)]
+        lib.fg_server_poll.restype = ctypes.c_int
+        lib.fg_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int]
+        lib.fg_server_wait.restype = ctypes.c_int
+        lib.fg_server_times.argtypes = [vp, ctypes.c_uint64, P(ctypes.c_double),
+                                        P(ctypes.c_double)]
+        lib.fg_server_times.restype = ctypes.c_int
+        lib.fg_server_release.argtypes = [vp, ctypes.c_uint64]
+        lib.fg_server_release.restype = ctypes.c_int
+        lib.fg_server_get_stats.argtypes = [vp, P(ServerStats)]
+        lib.fg_server_get_stats.restype = ctypes.c_int
+        lib.fg_server_destroy.argtypes = [vp]
+        lib.fg_server_destroy.restype = None
+        lib.fg_server_last_error.argtypes = []
+        lib.fg_server_last_error.restype = ctypes.c_char_p
+        lib._server_bound = True
+    return lib
+
+
+class Server:
+    """fg_server: continuous-batching job server on the current device. Jobs are host
+    tensors (I [H, W, 3], alpha [H, W], one float dtype); outputs are host tensors filled
+    when the job completes. Keep the tensors alive until then."""
+
+    def __init__(self, max_inflight_jobs=256, hbm_budget_bytes=0, streams=2, max_batch=64,
+                 p: Params | None = None):
+        lib = _server_lib()
+        cfg = ServerCfg()
+        lib.fg_server_cfg_default(ctypes.byref(cfg))
+        cfg.max_inflight_jobs = max_inflight_jobs
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        cfg.streams = streams
+        cfg.max_batch = max_batch
+        if p is not None:
+            cfg.params = p
+        h = ctypes.c_void_p()
+        st = lib.fg_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != FG_OK:
+            raise FgmlError(st, lib.fg_server_last_error().decode())
+        self._h = h
+        self._lib = lib
+        self._keep = {}
+
+    def _check(self, st):
+        if st != FG_OK:
+            raise FgmlError(st, self._lib.fg_server_last_error().decode())
+
+    def submit(self, I: torch.Tensor, alpha: torch.Tensor, F=None, B=None) -> int:
+        I = I.contiguous()
+        alpha = alpha.contiguous()
+        h, w = alpha.shape
+        if F is None:
+            F = torch.empty_like(I)
+        if B is None:
+            B = torch.empty_like(I)
+        r = Request(I.data_ptr(), alpha.data_ptr(), w, h, _DTYPES[I.dtype], F.data_ptr(),
+                    B.data_ptr())
+        t = ctypes.c_uint64()
+        self._check(self._lib.fg_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = (I, alpha, F, B)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        self._check(self._lib.fg_server_wait(self._h, ticket, timeout_ms))
+        _, _, F, B = self._keep[ticket]
+        return F, B
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        self._check(self._lib.fg_server_poll(self._h, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def times(self, ticket: int):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.fg_server_times(self._h, ticket, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def release(self, ticket: int):
+        self._check(self._lib.fg_server_release(self._h, ticket))
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        self._check(self._lib.fg_server_get_stats(self._h, ctypes.byref(s)))
+        return {n: getattr(s, n) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            self._lib.fg_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,102 @@
+"""Serving with continuous batching: jobs submitted while others run are admitted as slots
+and memory free up; each job's result is the same alone and in the mix (within the
+parity tolerance for float32, and a few units of the last place for 16-bit storage,
+where each level's F and B are rounded to the storage type)."""
+import random
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2006_14970_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float32: 1e-4, torch.bfloat16: 2 ** -6, torch.float16: 2 ** -9}
+
+
+def _alone(fgml, I, A):
+    F, B = fgml.estimate(I.cuda(), A.cuda())
+    torch.cuda.synchronize()
+    return F.cpu(), B.cpu()
+
+
+def _jobs(n, seed, lo=64, hi=900, dtypes=(torch.float32, torch.bfloat16)):
+    rng = random.Random(seed)
+    out = []
+    for i in range(n):
+        w = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        h = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        s = synth.make_sample(w, h, 3000 + seed + i)
+        dt = dtypes[i % len(dtypes)]
+        out.append((torch.from_numpy(s.I).to(dt).pin_memory(),
+                    torch.from_numpy(s.alpha).to(dt).pin_memory()))
+    return out
+
+
+def test_server_results_equal_alone_and_in_mix(fgml):
+    jobs = _jobs(24, 1)
+    with fgml.Server(streams=2, max_batch=8) as srv:
+        # submissions from two threads with small random gaps, so that jobs arrive while
+        # earlier batches run
+        tickets = [None] * len(jobs)
+
+        def feed(idx):
+            rng = random.Random(idx[0])
+            for i in idx:
+                tickets[i] = srv.submit(*jobs[i])
+                time.sleep(rng.uniform(0, 0.002))
+
+        th = [threading.Thread(target=feed, args=(list(range(k, len(jobs), 2)),)) for k in (0, 1)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        outs = [srv.wait(t, 60000) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    assert st["batches"] >= 2            # the work came in several batches
+    for (I, A), (F, B) in zip(jobs, outs):
+        Fa, Ba = _alone(fgml, I, A)
+        tol = TOL[I.dtype]
+        assert float((F.float() - Fa.float()).abs().max()) <= tol
+        assert float((B.float() - Ba.float()).abs().max()) <= tol
+
+
+def test_server_admission_by_memory_budget(fgml):
+    jobs = _jobs(10, 2, lo=300, hi=600, dtypes=(torch.float32,))
+    one = max(I.numel() * 4 * 13 // 3 + (1 << 20) for I, _ in jobs)
+    # room for about two jobs at a time: the rest wait in the queue instead of failing
+    with fgml.Server(hbm_budget_bytes=int(2.2 * one), streams=2, max_batch=4) as srv:
+        tickets = [srv.submit(I, A) for I, A in jobs]
+        outs = [srv.wait(t, 60000) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    assert st["max_bytes"] <= st["budget_bytes"]
+    assert st["max_inflight"] <= 2
+    for (I, A), (F, B) in zip(jobs, outs):
+        Fa, Ba = _alone(fgml, I, A)
+        assert float((F - Fa).abs().max()) <= TOL[torch.float32]
+
+
+def test_server_rejects_a_job_above_the_budget(fgml):
+    with fgml.Server(hbm_budget_bytes=1 << 20) as srv:
+        I = torch.zeros((512, 512, 3)).pin_memory()
+        A = torch.zeros((512, 512)).pin_memory()
+        with pytest.raises(fgml.FgmlError) as e:
+            srv.submit(I, A)
+        assert e.value.status == fgml.FG_ERR_INVALID_ARG
+
+
+def test_server_latency_records(fgml):
+    jobs = _jobs(6, 3, dtypes=(torch.float32,))
+    with fgml.Server() as srv:
+        t = [srv.submit(I, A) for I, A in jobs]
+        for x in t:
+            srv.wait(x, 60000)
+        for x in t:
+            a, b = srv.times(x)
+            assert 0 <= a <= b
+            srv.release(x)
