@@ -142,6 +142,106 @@ def cpu_baseline(sample: str, seconds: float = 10.0):
             "sample": f"{n} full FP64 solves of the {w}x{h} workload image ({dt:.1f} s)"}
 
 
+def batch_section(fgml, synth, torch, dev, timed, world, args):
+    """64 images with sides log-uniform in [256, 2048]: one fg_estimate_batch call against
+    the same images solved one at a time, both on device-resident inputs."""
+    ss = synth.batch(64)
+    imgs = [(torch.from_numpy(s.I).to(dev), torch.from_numpy(s.alpha).to(dev)) for s in ss]
+    outs = [(torch.empty_like(I), torch.empty_like(I)) for I, _ in imgs]
+    npx = sum(s.alpha.size for s in ss)
+    steps = max(3, args.steps // 4)
+    ms_b = timed(lambda: fgml.estimate_batch(imgs, None, outs), steps, args.warmup)
+
+    def one_by_one():
+        for (I, A), (F, B) in zip(imgs, outs):
+            fgml.estimate(I, A, None, F, B)
+    ms_1 = timed(one_by_one, steps, args.warmup)
+    return {"workload": "batch_64_uneven_256_2048_fp32", "images": len(ss), "pixels": int(npx),
+            "value": world * npx / (ms_b * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms_b,
+            "one_at_a_time": {"value": world * npx / (ms_1 * 1e-3) / 1e6, "unit": "Mpix/s",
+                              "ms_per_step": ms_1},
+            "launches_per_step": 2}
+
+
+def serving_section(fgml, synth, torch, args):
+    """Poisson arrivals of jobs (sides log-uniform in [256, 4096], random aspect, half
+    float32 and half bfloat16, host buffers) into the continuous-batching server, at
+    several multiples of the measured one-at-a-time float32 capacity."""
+    import threading
+    rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 4))
+    templates = []
+    for i in range(16):
+        w = int(np.exp(rng.uniform(np.log(256), np.log(4096))))
+        h = int(np.exp(rng.uniform(np.log(256), np.log(4096))))
+        s = synth.make_sample(w, h, synth.SEED_BASE + 400 + i)
+        dt = torch.float32 if i % 2 == 0 else torch.bfloat16
+        templates.append((torch.from_numpy(s.I).to(dt).pin_memory(),
+                          torch.from_numpy(s.alpha).to(dt).pin_memory(), w * h))
+    # one-at-a-time float32 capacity through the host-buffer entry point
+    f32 = [(I.float().pin_memory(), A.float().pin_memory(), n) for I, A, n in templates]
+    for I, A, _ in f32[:2]:
+        fgml.estimate_host(I, A)
+    t0 = time.perf_counter()
+    for I, A, _ in f32:
+        fgml.estimate_host(I, A)
+    dt1 = time.perf_counter() - t0
+    cap_req = len(f32) / dt1
+    cap_px = sum(n for _, _, n in f32) / dt1
+    out = {"workload": "serving_poisson_256_4096_mixed_f32_bf16",
+           "one_at_a_time_f32": {"req_s": cap_req, "mpix_s": cap_px / 1e6}, "rates": []}
+    n_req = max(16, args.serving_requests)
+    for x in (0.5, 0.9, 1.2):
+        rate = x * cap_req
+        gaps = rng.exponential(1.0 / rate, n_req)
+        picks = rng.integers(0, len(templates), n_req)
+        with fgml.Server(streams=2, max_batch=32) as srv:
+            tickets, done, subs, lat = [], [], [], []
+            lock = threading.Lock()
+            finished = threading.Event()
+
+            def collect():
+                k = 0
+                while k < n_req:
+                    with lock:
+                        have = len(tickets)
+                    if k >= have:
+                        time.sleep(0.0002)
+                        continue
+                    t = tickets[k]
+                    srv.wait(t, 120000)
+                    a, b = srv.times(t)
+                    lat.append(b - a)
+                    done.append(b)
+                    subs.append(a)
+                    srv.release(t)
+                    k += 1
+                finished.set()
+
+            th = threading.Thread(target=collect)
+            th.start()
+            start = time.perf_counter()
+            at = 0.0
+            for g, k in zip(gaps, picks):
+                at += g
+                while time.perf_counter() - start < at:
+                    pass
+                I, A, _ = templates[k]
+                t = srv.submit(I, A)
+                with lock:
+                    tickets.append(t)
+            finished.wait()
+            th.join()
+            st = srv.stats()
+        span = max(done) - min(subs)   # from the first arrival to the last completion
+        px = st["pixels"]
+        lat_ms = np.array(lat) * 1e3
+        out["rates"].append({"x_capacity": x, "offered_req_s": rate, "requests": n_req,
+                             "mpix_s": px / span / 1e6, "p50_ms": float(np.percentile(lat_ms, 50)),
+                             "p99_ms": float(np.percentile(lat_ms, 99)), "batches": st["batches"],
+                             "max_inflight": st["max_inflight"]})
+    return out
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -167,6 +267,9 @@ def main():
     ap.add_argument("--impl", default="fgml", choices=["fgml", "reference"])
     ap.add_argument("--no-8k", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -297,6 +400,13 @@ def main():
                                     "max_abs_vs_f32_path": d}
             del I16, A16, F16, B16
 
+    batch = None
+    if not args.no_batch:
+        batch = batch_section(fgml, synth, torch, dev, timed, world, args)
+    serving = None
+    if not args.no_serving:
+        serving = serving_section(fgml, synth, torch, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(WORKLOAD)
@@ -310,7 +420,8 @@ def main():
                            "levels": len(levels), "l2": "flushed before every timed step",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-                "clocks": clocks, "cpu_baseline": cpu, "big": big,
+                "clocks": clocks, "cpu_baseline": cpu, "big": big, "batch": batch,
+                "serving": serving,
                 "library": fgml.version()}
         print(json.dumps(line), flush=True)
     if world > 1:

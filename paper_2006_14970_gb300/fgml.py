@@ -334,10 +334,11 @@ class Server:
         I = I.contiguous()
         alpha = alpha.contiguous()
         h, w = alpha.shape
+        pin = I.is_pinned()
         if F is None:
-            F = torch.empty_like(I)
+            F = torch.empty(I.shape, dtype=I.dtype, pin_memory=pin)
         if B is None:
-            B = torch.empty_like(I)
+            B = torch.empty(I.shape, dtype=I.dtype, pin_memory=pin)
         r = Request(I.data_ptr(), alpha.data_ptr(), w, h, _DTYPES[I.dtype], F.data_ptr(),
                     B.data_ptr())
         t = ctypes.c_uint64()
