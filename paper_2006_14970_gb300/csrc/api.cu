@@ -210,6 +210,7 @@ struct State {
     const void *F, *B;
     long long pitch;   // elements
     int w, h;
+    bool padded;       // rows are padded to 16 bytes inside the allocation (workspace)
 };
 
 // Rows of a workspace state are padded to 16 bytes so that tensor copies can read them.
@@ -231,6 +232,7 @@ State state_in(const Buf &b, int w, int h, int es) {
     s.pitch = state_pitch(w, es);
     s.w = w;
     s.h = h;
+    s.padded = true;
     return s;
 }
 
@@ -280,52 +282,59 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// A 2D tensor map of `rows` rows of `inner` elements, `pitch` bytes apart; false if the
-// layout does not allow tensor copies (base or pitch off the 16-byte grid).
-bool make_map(CUtensorMap *m, int dtype, const void *base, long long inner, long long rows,
-              long long pitch, int box_x, int box_y) {
+// A 2D tensor map of `rows` rows of `inner8` 8-byte elements, `pitch` bytes apart, with
+// a one-row box of `box8` elements (for gather-mode copies); false if the layout does
+// not allow tensor copies (base or pitch off the 16-byte grid, box too wide).
+bool make_map(CUtensorMap *m, const void *base, long long inner8, long long rows, long long pitch,
+              int box8) {
     EncodeTiledFn fn = encode_tiled();
-    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (pitch & 15) || box_x > 256 ||
-        box_y > 256 || box_x < 1 || box_y < 1)
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (pitch & 15) || box8 > 256 || box8 < 2 ||
+        (box8 & 1) || inner8 < 1 || inner8 * 8 > pitch)
         return false;
-    const CUtensorMapDataType dt = dtype == kF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                   : dtype == kBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    const cuuint64_t dims[2] = {(cuuint64_t)inner8, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-    const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+    const cuuint32_t box[2] = {(cuuint32_t)box8, 1};
     const cuuint32_t estr[2] = {1, 1};
-    return fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Fills the tile-variant fields of `a` and builds its maps; false if not applicable.
 bool plan_tile(int dtype, const Input &in, const State &src, PassArgs &a, TileMaps &m) {
-    if (in.w != a.w || in.h != a.h) return false;   // I and alpha must be the input itself
     const int es = dtype == kF32 ? 4 : 2;
-    const int q = 16 / es, R = level_pass_tile_rows();
     auto up = [](int v, int k) { return (v + k - 1) / k * k; };
     auto r128 = [](int v) { return (v + 127) & ~127; };
-    a.tile_bwI = up(3 * 64 + q - 1, q);
-    a.tile_bwA = up(64 + q - 1, q);
-    a.tile_bwS = up(3 * strip_span(src.w, a.w) + q - 1, q);
-    int rs = 1;
-    for (int r0 = 0; r0 < a.h; ++r0) {
-        const int r1 = std::min(r0 + R - 1, a.h - 1);
-        rs = std::max(rs, nearest_src(r1, src.h, a.h) - nearest_src(r0, src.h, a.h) + 1);
+    const int spanI = strip_span(in.w, a.w), spanS = strip_span(src.w, a.w);
+    a.tile_bwI = up((15 + 3 * spanI * es + 7) / 8, 2);
+    a.tile_bwA = up((15 + spanI * es + 7) / 8, 2);
+    a.tile_bwS = up((15 + 3 * spanS * es + 7) / 8, 2);
+    if (a.tile_bwI > 256 || a.tile_bwA > 256 || a.tile_bwS > 256) return false;
+    // rows as whole 8-byte elements: exact for I and alpha; for a padded workspace
+    // state the last partial element lies inside the row's padding
+    const long long rbI = 3LL * in.w * es, rbA = (long long)in.w * es, rbS = 3LL * src.w * es;
+    if (rbI % 8 || rbA % 8) return false;
+    long long inS = rbS / 8;
+    if (rbS % 8) {
+        if (!src.padded || (rbS + 7) / 8 * 8 > src.pitch * es) return false;
+        inS = (rbS + 7) / 8;
     }
-    a.tile_rs = rs;
-    a.tile_offA = r128(R * a.tile_bwI * es);
-    a.tile_offF = a.tile_offA + r128(R * a.tile_bwA * es);
-    a.tile_offB = a.tile_offF + r128(rs * a.tile_bwS * es);
-    a.tile_chunk = a.tile_offB + r128(rs * a.tile_bwS * es);
-    a.tile_tx = R * (a.tile_bwI + a.tile_bwA) * es + 2 * rs * a.tile_bwS * es;
-    if (level_pass_tile_smem(a.tile_chunk) > kRingSmemBudget) return false;
-    return make_map(&m.I, dtype, in.I, 3LL * in.w, in.h, in.I_pitch * es, a.tile_bwI, R) &&
-           make_map(&m.A, dtype, in.A, in.w, in.h, in.A_pitch * es, a.tile_bwA, R) &&
-           make_map(&m.F, dtype, src.F, 3LL * src.w, src.h, src.pitch * es, a.tile_bwS, rs) &&
-           make_map(&m.B, dtype, src.B, 3LL * src.w, src.h, src.pitch * es, a.tile_bwS, rs);
+    const int R = level_pass_tile_rows();
+    a.tile_offA = r128(R * a.tile_bwI * 8);
+    a.tile_offF = a.tile_offA + r128(R * a.tile_bwA * 8);
+    a.tile_offB = a.tile_offF + r128(R * a.tile_bwS * 8);
+    a.tile_chunk = a.tile_offB + r128(R * a.tile_bwS * 8);
+    a.tile_tx = R * 8 * (a.tile_bwI + a.tile_bwA + 2 * a.tile_bwS);
+    if (level_pass_tile_smem(a.tile_chunk, 3) <= kRingSmemBudget)
+        a.tile_slots = 3;
+    else if (level_pass_tile_smem(a.tile_chunk, 2) <= kRingSmemBudget)
+        a.tile_slots = 2;
+    else
+        return false;
+    return make_map(&m.I, in.I, rbI / 8, in.h, in.I_pitch * es, a.tile_bwI) &&
+           make_map(&m.A, in.A, rbA / 8, in.h, in.A_pitch * es, a.tile_bwA) &&
+           make_map(&m.F, src.F, inS, src.h, src.pitch * es, a.tile_bwS) &&
+           make_map(&m.B, src.B, inS, src.h, src.pitch * es, a.tile_bwS);
 }
 
 cudaError_t pass(int dtype, int iters, int clamp, const fg_params &p, const Input &in,
@@ -692,7 +701,7 @@ fg_status fg_level_pass(const fg_image *I, const fg_image *alpha, const fg_image
     const int es = elem_size(dt);
     cudaStream_t s = (cudaStream_t)stream;
     Input in{I->ptr, alpha->ptr, I->row_pitch_bytes / es, alpha->row_pitch_bytes / es, I->w, I->h};
-    State src{F_src->ptr, B_src->ptr, F_src->row_pitch_bytes / es, F_src->w, F_src->h};
+    State src{F_src->ptr, B_src->ptr, F_src->row_pitch_bytes / es, F_src->w, F_src->h, false};
     const int w = F_dst->w, h = F_dst->h;
     Workspace &ws = workspace_for(s);
     if (split_sweeps(iters).size() > 1) {

@@ -57,8 +57,8 @@ struct PassArgs {
     int capI, capA, capS, slot_bytes;
     // row-ring variant only: one past the last byte of I, alpha, Fs and Bs
     const void *I_end, *A_end, *Fs_end, *Bs_end;
-    // tile variant only: box widths (elements), source rows per chunk, chunk layout (bytes)
-    int tile_bwI, tile_bwA, tile_bwS, tile_rs;
+    // tile variant only: box widths (8-byte elements), chunk layout (bytes), chunks in flight
+    int tile_bwI, tile_bwA, tile_bwS, tile_slots;
     int tile_offA, tile_offF, tile_offB, tile_chunk, tile_tx;
 };
 
@@ -91,7 +91,7 @@ cudaError_t launch_level_batch(int dtype, int clamp, const BatchLaunch &b, cudaS
                                int *blocks_per_sm);
 
 // Tensor maps of the tile variant: I, alpha, and the starting F and B, as 2D tensors of
-// elements (row length = channels x width).
+// 8-byte elements (a row's bytes / 8), box one row high for gather-mode copies.
 struct TileMaps {
     CUtensorMap I, A, F, B;
 };
@@ -135,7 +135,7 @@ size_t level_pass_ring_smem(int slot_bytes);
 // full-resolution input; a.tile_* must be filled in and the maps built for them.
 cudaError_t launch_level_pass_tile(int dtype, int iters, int clamp, const PassArgs &a,
                                    const TileMaps &m, cudaStream_t s);
-size_t level_pass_tile_smem(int chunk_bytes);
+size_t level_pass_tile_smem(int chunk_bytes, int slots);
 // Small-level variant: one block per 32 x 16 output tile, all sweeps in shared memory.
 cudaError_t launch_level_small(int dtype, int iters, int clamp, const PassArgs &a,
                                cudaStream_t s);

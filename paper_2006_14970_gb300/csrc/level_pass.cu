@@ -41,8 +41,7 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kLaneCols = 64;        // columns held by a warp (2 per lane)
 constexpr int kWaitPolls = 1 << 20;          // try_wait polls before a wait gives up
 constexpr uint32_t kWaitHintNs = 2000;       // suspend-time hint of one poll
-constexpr int kTileRows = 4;                 // rows per tensor-copy chunk
-constexpr int kTileSlots = 3;                // chunks in flight per warp
+constexpr int kTileRows = 4;                 // rows per tensor-copy chunk (gather mode: 4)
 #ifndef FGML_RING_MIN_BLOCKS
 #define FGML_RING_MIN_BLOCKS 2
 #endif
@@ -635,53 +634,70 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kRingMinBlocks) level_pas
     run_strip<T, K, CLAMP>(p, g, ct, out, src);
 }
 
-// Tile variant (top level, where I and alpha are the input itself): the warp's rows
-// arrive in chunks of kTileRows rows, each chunk fetched by four 2D tensor copies (boxes
-// of I, alpha, F and B rows; the hardware forms the addresses and fills zeros outside the
-// images), kTileSlots chunks in flight per warp. Ring bookkeeping is paid once per chunk.
-template <typename T>
+// Tile variant: the warp's rows arrive in chunks of kTileRows rows. A chunk is four
+// tensor copies in gather mode, each fetching the chunk's kTileRows rows of one image
+// (I, alpha, F or B) by row index: the nearest-resize source rows of the chunk's output
+// rows (Algorithm 1), so the same kernel serves the top level (I and alpha rows are the
+// input rows) and gathered levels. The tensors are viewed as rows of 8-byte elements, so
+// one box of at most 256 elements holds a strip's source span; the hardware forms the
+// addresses and fills zeros outside the images. SLOTS chunks are in flight per warp; the
+// ring bookkeeping is paid once per chunk.
+template <typename T, int SLOTS>
 struct TileSource {
+    const unsigned char *sm;   // the block's shared memory, and its shared address
+    uint32_t sbase;
     uint32_t slots_s, bar0;
     int lane;
     const CUtensorMap *mI, *mA, *mF, *mB;
-    int xI, xA, xS;         // box x coordinates (elements; multiples of 16 bytes)
-    int li, la, ls, dI, dS; // per-lane element offsets inside box rows
+    int xI, xA, xS;         // box x coordinates (8-byte elements; even)
+    int oI0, oI1, oA0, oA1, oS0, oS1;   // per-lane byte offsets of the two pixels in box rows
     int r_first;
     int cfill;              // next chunk to fill
     int j;                  // row of the current chunk being taken
     int gslot;              // slot of the current chunk
     uint32_t gpar;
-    int sy0;                // first source F/B row of the current chunk
     uint32_t issued, parity;
-    RowMap gS;              // source F/B row of the next row to take
+    RowMap fI, fS;          // source rows of the next row to fill
 
-    __device__ __forceinline__ void fill(const PassArgs &p) {
-        const int r0 = r_first + cfill * kTileRows;
-        const int slot = cfill % kTileSlots;
-        const uint32_t par = (uint32_t)(cfill / kTileSlots) & 1u;
+    __device__ __forceinline__ void fill(const PassArgs &p, const Ctl &ct) {
+        const int slot = cfill % SLOTS;
+        const uint32_t par = (uint32_t)(cfill / SLOTS) & 1u;
+        // source rows of the chunk's rows (rows past the strip repeat its last row)
+        int gy[kTileRows], sy[kTileRows];
+#pragma unroll
+        for (int k = 0; k < kTileRows; ++k) {
+            const int r = r_first + cfill * kTileRows + k;
+            if (r <= ct.r_last) {
+                gy[k] = fI.next();
+                sy[k] = fS.next();
+            } else {
+                gy[k] = gy[k > 0 ? k - 1 : 0];
+                sy[k] = sy[k > 0 ? k - 1 : 0];
+            }
+        }
         if (lane == 0) {
             const uint32_t dst = slots_s + (uint32_t)slot * (uint32_t)p.tile_chunk;
             const uint32_t bar = bar0 + 8u * (uint32_t)slot;
-            const int sy = nearest_src(r0, p.sh, p.h);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                          :: "r"(bar), "r"((uint32_t)p.tile_tx) : "memory");
-            tile_copy(dst, mI, xI, r0, bar);
-            tile_copy(dst + (uint32_t)p.tile_offA, mA, xA, r0, bar);
-            tile_copy(dst + (uint32_t)p.tile_offF, mF, xS, sy, bar);
-            tile_copy(dst + (uint32_t)p.tile_offB, mB, xS, sy, bar);
+            gather4(dst, mI, xI, gy, bar);
+            gather4(dst + (uint32_t)p.tile_offA, mA, xA, gy, bar);
+            gather4(dst + (uint32_t)p.tile_offF, mF, xS, sy, bar);
+            gather4(dst + (uint32_t)p.tile_offB, mB, xS, sy, bar);
         }
         issued |= 1u << slot;
         parity = (parity & ~(1u << slot)) | (par << slot);
         ++cfill;
     }
 
-    __device__ __forceinline__ static void tile_copy(uint32_t dst, const CUtensorMap *m, int x,
-                                                     int y, uint32_t bar) {
+    __device__ __forceinline__ static void gather4(uint32_t dst, const CUtensorMap *m, int x,
+                                                   const int *y, uint32_t bar) {
         asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3}], [%4];"
-            :: "r"(dst), "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(bar)
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+            :: "r"(dst), "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y[0]), "r"(y[1]),
+               "r"(y[2]), "r"(y[3]), "r"(bar)
             : "memory");
     }
 
@@ -705,13 +721,12 @@ struct TileSource {
         gslot = 0;
         gpar = 0;
         issued = parity = 0;
-        gS.init(ct.r_first, p.sh, p.h);
+        fI.init(ct.r_first, p.Ih, p.h);
+        fS.init(ct.r_first, p.sh, p.h);
         const int nchunks = (ct.r_last - ct.r_first) / kTileRows + 1;
-        for (int c = 0; c < kTileSlots && c < nchunks; ++c) fill(p);
+        for (int c = 0; c < SLOTS && c < nchunks; ++c) fill(p, ct);
     }
 
-    const unsigned char *sm;   // the block's shared memory, and its shared address
-    uint32_t sbase;
     template <typename U>
     __device__ __forceinline__ float lds(uint32_t a) const {
         return to_f(*reinterpret_cast<const U *>(sm + (a - sbase)));
@@ -722,32 +737,30 @@ struct TileSource {
         if (j == 0) {
             if (!wait(gslot, gpar)) return false;
             issued &= ~(1u << gslot);
-            sy0 = nearest_src(r, p.sh, p.h);
         }
         const int es = (int)sizeof(T);
-        const int sy = gS.next();
         const uint32_t base = slots_s + (uint32_t)gslot * (uint32_t)p.tile_chunk;
-        const uint32_t I = base + (uint32_t)((j * p.tile_bwI + li) * es);
-        const uint32_t A = base + (uint32_t)p.tile_offA + (uint32_t)((j * p.tile_bwA + la) * es);
-        const uint32_t F = base + (uint32_t)p.tile_offF + (uint32_t)(((sy - sy0) * p.tile_bwS + ls) * es);
-        const uint32_t B = base + (uint32_t)p.tile_offB + (uint32_t)(((sy - sy0) * p.tile_bwS + ls) * es);
-        o.a0 = lds<T>(A);
-        o.a1 = lds<T>(A + dI * es);
+        const uint32_t I = base + (uint32_t)(j * p.tile_bwI * 8);
+        const uint32_t A = base + (uint32_t)p.tile_offA + (uint32_t)(j * p.tile_bwA * 8);
+        const uint32_t F = base + (uint32_t)p.tile_offF + (uint32_t)(j * p.tile_bwS * 8);
+        const uint32_t B = base + (uint32_t)p.tile_offB + (uint32_t)(j * p.tile_bwS * 8);
+        o.a0 = lds<T>(A + oA0);
+        o.a1 = lds<T>(A + oA1);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            o.i0[c] = lds<T>(I + c * es);
-            o.i1[c] = lds<T>(I + (3 * dI + c) * es);
-            o.f0[c] = lds<T>(F + c * es);
-            o.f1[c] = lds<T>(F + (3 * dS + c) * es);
-            o.b0[c] = lds<T>(B + c * es);
-            o.b1[c] = lds<T>(B + (3 * dS + c) * es);
+            o.i0[c] = lds<T>(I + oI0 + c * es);
+            o.i1[c] = lds<T>(I + oI1 + c * es);
+            o.f0[c] = lds<T>(F + oS0 + c * es);
+            o.f1[c] = lds<T>(F + oS1 + c * es);
+            o.b0[c] = lds<T>(B + oS0 + c * es);
+            o.b1[c] = lds<T>(B + oS1 + c * es);
         }
         if (++j == kTileRows || r == ct.r_last) {
-            // the chunk is used up: refill its slot with the chunk kTileSlots ahead
+            // the chunk is used up: refill its slot with the chunk SLOTS ahead
             __syncwarp();
             j = 0;
-            if (r_first + cfill * kTileRows <= ct.r_last) fill(p);
-            if (++gslot == kTileSlots) {
+            if (r_first + cfill * kTileRows <= ct.r_last) fill(p, ct);
+            if (++gslot == SLOTS) {
                 gslot = 0;
                 gpar ^= 1u;
             }
@@ -756,12 +769,12 @@ struct TileSource {
     }
 
     __device__ __forceinline__ void abort() const {
-        for (int s = 0; s < kTileSlots; ++s)
+        for (int s = 0; s < SLOTS; ++s)
             if (issued & (1u << s)) wait(s, (parity >> s) & 1u);
     }
 };
 
-template <typename T, int K, bool CLAMP>
+template <typename T, int K, bool CLAMP, int SLOTS>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_tile_kernel(
     const PassArgs p, const __grid_constant__ CUtensorMap mI, const __grid_constant__ CUtensorMap mA,
     const __grid_constant__ CUtensorMap mF, const __grid_constant__ CUtensorMap mB) {
@@ -775,7 +788,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_tile_kernel
     Out out;
     lane_setup<T>(p, warp, lane, g, ct, out, K);
 
-    TileSource<T> src;
+    TileSource<T, SLOTS> src;
     src.sm = smem;
     src.sbase = smem_addr(smem);
     src.lane = lane;
@@ -783,28 +796,26 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_tile_kernel
     src.mA = &mA;
     src.mF = &mF;
     src.mB = &mB;
-    src.slots_s = smem_addr(smem) + (uint32_t)(wib * kTileSlots * p.tile_chunk);
-    src.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * kTileSlots * p.tile_chunk) +
-               8u * (uint32_t)(wib * kTileSlots);
-    // box x coordinates: the strip's first column rounded down to 16 bytes (may be
-    // negative; the copy then fills zeros there)
-    const int q = 16 / (int)sizeof(T);
+    src.slots_s = smem_addr(smem) + (uint32_t)(wib * SLOTS * p.tile_chunk);
+    src.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * SLOTS * p.tile_chunk) +
+               8u * (uint32_t)(wib * SLOTS);
+    // the strip's source column ranges; box x is the first source byte rounded down to 16
+    const int es = (int)sizeof(T);
     const int X0 = g.x - 2 * lane;
-    auto floor_q = [q](int v) { return v >= 0 ? v / q * q : -((-v + q - 1) / q) * q; };
-    src.xI = floor_q(3 * X0);
-    src.xA = floor_q(X0);
     const int xf = min(max(X0, 0), p.w - 1);
+    const int giF = nearest_src(xf, p.Iw, p.w);
     const int gsF = nearest_src(xf, p.sw, p.w);
-    src.xS = floor_q(3 * gsF);
-    // the lanes read their own columns; outside the image those are zero-filled
-    // (weights ignore them)
-    src.li = 3 * g.x - src.xI;
-    src.la = g.x - src.xA;
-    src.dI = 1;
-    src.ls = 3 * g.gs0 - src.xS;
-    src.dS = g.gs1 - g.gs0;
+    src.xI = (3 * giF * es) / 16 * 2;
+    src.xA = (giF * es) / 16 * 2;
+    src.xS = (3 * gsF * es) / 16 * 2;
+    src.oI0 = 3 * g.gi0 * es - 8 * src.xI;
+    src.oI1 = 3 * g.gi1 * es - 8 * src.xI;
+    src.oA0 = g.gi0 * es - 8 * src.xA;
+    src.oA1 = g.gi1 * es - 8 * src.xA;
+    src.oS0 = 3 * g.gs0 * es - 8 * src.xS;
+    src.oS1 = 3 * g.gs1 * es - 8 * src.xS;
     if (lane == 0) {
-        for (int s = 0; s < kTileSlots; ++s)
+        for (int s = 0; s < SLOTS; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(src.bar0 + 8u * s) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -959,22 +970,27 @@ cudaError_t launch_ring_t(const PassArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <typename T, int K, bool CLAMP>
+template <typename T, int K, bool CLAMP, int SLOTS>
 cudaError_t launch_tile_t(const PassArgs &a, const TileMaps &m, cudaStream_t s) {
     const int blocks = (a.n_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const size_t smem = level_pass_tile_smem(a.tile_chunk);
-    cudaError_t e = cudaFuncSetAttribute(level_pass_tile_kernel<T, K, CLAMP>,
+    const size_t smem = level_pass_tile_smem(a.tile_chunk, SLOTS);
+    cudaError_t e = cudaFuncSetAttribute(level_pass_tile_kernel<T, K, CLAMP, SLOTS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    level_pass_tile_kernel<T, K, CLAMP><<<blocks, kWarpsPerBlock * 32, smem, s>>>(a, m.I, m.A, m.F, m.B);
+    level_pass_tile_kernel<T, K, CLAMP, SLOTS><<<blocks, kWarpsPerBlock * 32, smem, s>>>(a, m.I, m.A, m.F, m.B);
     return cudaGetLastError();
+}
+
+template <typename T, int K, bool CLAMP>
+cudaError_t launch_tile_slots(const PassArgs &a, const TileMaps &m, cudaStream_t s) {
+    return a.tile_slots == 3 ? launch_tile_t<T, K, CLAMP, 3>(a, m, s) : launch_tile_t<T, K, CLAMP, 2>(a, m, s);
 }
 
 template <typename T>
 cudaError_t launch_tile_dtype(int iters, int clamp, const PassArgs &a, const TileMaps &m,
                               cudaStream_t s) {
-    if (iters == 1) return clamp ? launch_tile_t<T, 1, true>(a, m, s) : launch_tile_t<T, 1, false>(a, m, s);
-    if (iters == 2) return clamp ? launch_tile_t<T, 2, true>(a, m, s) : launch_tile_t<T, 2, false>(a, m, s);
+    if (iters == 1) return clamp ? launch_tile_slots<T, 1, true>(a, m, s) : launch_tile_slots<T, 1, false>(a, m, s);
+    if (iters == 2) return clamp ? launch_tile_slots<T, 2, true>(a, m, s) : launch_tile_slots<T, 2, false>(a, m, s);
     return cudaErrorInvalidValue;
 }
 
@@ -1033,9 +1049,8 @@ cudaError_t launch_level_pass_tile(int dtype, int iters, int clamp, const PassAr
     return cudaErrorInvalidValue;
 }
 
-size_t level_pass_tile_smem(int chunk_bytes) {
-    return (size_t)kWarpsPerBlock * kTileSlots * (size_t)chunk_bytes +
-           (size_t)kWarpsPerBlock * kTileSlots * 8;
+size_t level_pass_tile_smem(int chunk_bytes, int slots) {
+    return (size_t)kWarpsPerBlock * slots * (size_t)chunk_bytes + (size_t)kWarpsPerBlock * slots * 8;
 }
 
 int level_pass_tile_rows() { return kTileRows; }
