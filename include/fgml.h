@@ -117,7 +117,9 @@ fg_status fg_estimate_host(const void *I, const void *alpha, int w, int h, fg_dt
  * and alpha (Algorithm 1: resize from the input); the starting F and B are the nearest
  * resize of (F_src, B_src) (a previous level, or this level itself); `iters` Jacobi
  * sweeps (1..2 per pass, >2 runs several passes through the workspace) are written to
- * (F_dst, B_dst), which must be w x h and must not overlap F_src/B_src.
+ * (F_dst, B_dst), which must be w x h and must not overlap F_src/B_src. F_src and B_src
+ * must each be readable over h x row_pitch_bytes bytes (the last row's padding too, as
+ * with a pitched allocation).
  */
 fg_status fg_level_pass(const fg_image *I, const fg_image *alpha,
                         const fg_image *F_src, const fg_image *B_src,

@@ -244,18 +244,26 @@ struct Input {
     int w, h;
 };
 
-// Rows per warp of a level pass: enough warps for several waves of resident warps.
+// Rows per warp of a level pass: one wave of resident warps (two 4-warp blocks per SM)
+// when the level is wide enough, so that every warp walks one tall strip and the
+// vertical halo (2 rows above and below each strip) stays a small fraction.
 int strip_rows(int w, int h) {
     const int nx = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
-    const long long target = (long long)sm_count() * 48;   // ~4 waves of 12 warps per SM
-    long long r = ((long long)h * nx + target - 1) / target;
-    r = std::max<long long>(r, 4);
-    r = std::min<long long>(r, 512);
-    return (int)r;
+    const long long resident = (long long)sm_count() * 2 * level_pass_warps_per_block();
+    const long long ny = std::max<long long>(1, resident / nx);
+    long long r = (h + ny - 1) / ny;
+    return (int)std::max<long long>(r, 1);
 }
 
-// Levels up to this many pixels run in the small-level kernel (latency bound).
-constexpr long long kSmallLevelPixels = 300000;
+// Levels up to this many pixels run in the small-level kernel (latency bound);
+// FGML_SMALL_LEVEL_PIXELS overrides it for tuning.
+long long small_level_pixels() {
+    static const long long v = [] {
+        const char *e = std::getenv("FGML_SMALL_LEVEL_PIXELS");
+        return e && *e ? std::atoll(e) : 2500000LL;
+    }();
+    return v;
+}
 
 // Shared memory of one ring- or tile-variant block; two blocks must fit on an SM.
 constexpr size_t kRingSmemBudget = 110 * 1024;
@@ -363,7 +371,7 @@ cudaError_t pass(int dtype, int iters, int clamp, const fg_params &p, const Inpu
     a.n_xstrips = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
     a.n_warps = a.n_xstrips * ((h + a.strip_h - 1) / a.strip_h);
     a.capI = a.capA = a.capS = a.slot_bytes = 0;
-    if ((iters == 1 || iters == 2) && (long long)w * h <= kSmallLevelPixels)
+    if ((iters == 1 || iters == 2) && (long long)w * h <= small_level_pixels())
         return launch_level_small(dtype, iters, clamp, a, s);
     if (iters == 1 || iters == 2) {
         TileMaps maps;
@@ -701,7 +709,8 @@ fg_status fg_level_pass(const fg_image *I, const fg_image *alpha, const fg_image
     const int es = elem_size(dt);
     cudaStream_t s = (cudaStream_t)stream;
     Input in{I->ptr, alpha->ptr, I->row_pitch_bytes / es, alpha->row_pitch_bytes / es, I->w, I->h};
-    State src{F_src->ptr, B_src->ptr, F_src->row_pitch_bytes / es, F_src->w, F_src->h, false};
+    // the sources' rows are readable up to their pitch, the last row included
+    State src{F_src->ptr, B_src->ptr, F_src->row_pitch_bytes / es, F_src->w, F_src->h, true};
     const int w = F_dst->w, h = F_dst->h;
     Workspace &ws = workspace_for(s);
     if (split_sweeps(iters).size() > 1) {
