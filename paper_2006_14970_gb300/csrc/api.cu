@@ -260,7 +260,7 @@ int strip_rows(int w, int h) {
 long long small_level_pixels() {
     static const long long v = [] {
         const char *e = std::getenv("FGML_SMALL_LEVEL_PIXELS");
-        return e && *e ? std::atoll(e) : 2500000LL;
+        return e && *e ? std::atoll(e) : 300000LL;
     }();
     return v;
 }

@@ -486,19 +486,23 @@ struct RingSource {
 // (K == 2) sweep 2 at row r-2. Queue arguments are the rows r, r-1, r-2 (S: row data,
 // Q: starting state) and r-1, r-2, r-3 (P: sweep-1 state). Returns false if a bounded
 // wait gave up.
-template <typename T, int K, bool CLAMP, typename Src>
+//
+// STEADY: every stage is active and no image border is involved (the caller checks the
+// row range), so the step runs without guards and its stages form one basic block that
+// the compiler can interleave.
+template <typename T, int K, bool CLAMP, bool STEADY, typename Src>
 __device__ __forceinline__ bool step(const PassArgs &p, const LaneGeo &g, const Ctl &ct,
                                      const Out &out, int r, Src &src, RowK &Sr, RowK &Sr1,
                                      RowK &Sr2, FB &Qr, FB &Qr1, FB &Qr2, FB &Pw, FB &Pr2,
                                      FB &Pr3) {
-    if (r <= ct.r_last) {
+    if (STEADY || r <= ct.r_last) {
         Raw cur;
         if (!src.get(p, g, ct, r, cur)) return false;
-        make_row(cur, g, r, Sr1, p.eps, p.omega, Sr, Qr);
+        make_row(cur, g, STEADY ? 1 : r, Sr1, p.eps, p.omega, Sr, Qr);
     }
     const int q = r - 1;
-    if (q >= ct.r_first && q <= ct.r_last) {
-        if (q < p.h - 1) {
+    if (STEADY || (q >= ct.r_first && q <= ct.r_last)) {
+        if (STEADY || q < p.h - 1) {
             Sr1.wd = Sr.wu;          // the edge (q, q+1) seen from row q
         } else {
             Sr1.wd = f2(0.f, 0.f);   // bottom row: the neighbour below is the pixel itself
@@ -507,21 +511,32 @@ __device__ __forceinline__ bool step(const PassArgs &p, const LaneGeo &g, const 
         finish_row(Sr1);
     }
     if (K == 1) {
-        if (q >= ct.Y0 && q < ct.Y1) {
+        if (STEADY || (q >= ct.Y0 && q < ct.Y1)) {
             FB res;
             update<CLAMP>(Sr1, Qr1, Qr2, Qr, res);
             store_row<T>(out, q, res);
         }
     } else {
-        if (q >= ct.t1_lo && q <= ct.t1_hi) update<CLAMP>(Sr1, Qr1, Qr2, Qr, Pw);
+        if (STEADY || (q >= ct.t1_lo && q <= ct.t1_hi)) update<CLAMP>(Sr1, Qr1, Qr2, Qr, Pw);
         const int q2 = r - 2;
-        if (q2 >= ct.Y0 && q2 < ct.Y1) {
+        if (STEADY || (q2 >= ct.Y0 && q2 < ct.Y1)) {
             FB res;
             update<CLAMP>(Sr2, Pr2, Pr3, Pw, res);
             store_row<T>(out, q2, res);
         }
     }
     return true;
+}
+
+// Rows r whose step has every stage active and touches no image border.
+__device__ __forceinline__ void steady_range(const Ctl &ct, int K, int &lo, int &hi) {
+    if (K == 1) {
+        lo = max(max(ct.r_first + 1, ct.Y0 + 1), 1);
+        hi = min(ct.r_last, ct.Y1);
+    } else {
+        lo = max(max(ct.r_first + 2, ct.t1_lo + 1), max(ct.Y0 + 2, 1));
+        hi = min(ct.r_last, min(ct.t1_hi + 1, ct.Y1 + 1));
+    }
 }
 
 __device__ __forceinline__ void zero(FB &v) {
@@ -574,14 +589,21 @@ __device__ __forceinline__ bool run_strip(const PassArgs &p, const LaneGeo &g, c
     zero(P0); zero(P1); zero(P2);
     src.start(p, g, ct);
     const int r_end = ct.r_last + K;
+    int s_lo, s_hi;
+    steady_range(ct, K, s_lo, s_hi);
     bool ok = true;
+#define FGML_STEP(R, A, B, C, D, E, F, G, H, I)                                                      \
+    ((R) >= s_lo && (R) <= s_hi                                                                      \
+         ? step<T, K, CLAMP, true>(p, g, ct, out, (R), src, A, B, C, D, E, F, G, H, I)               \
+         : step<T, K, CLAMP, false>(p, g, ct, out, (R), src, A, B, C, D, E, F, G, H, I))
     for (int r = ct.r_first; r <= r_end && ok; r += 3) {
-        ok = step<T, K, CLAMP>(p, g, ct, out, r, src, S0, S2, S1, Q0, Q2, Q1, P2, P1, P0);
+        ok = FGML_STEP(r, S0, S2, S1, Q0, Q2, Q1, P2, P1, P0);
         if (!ok || r + 1 > r_end) break;
-        ok = step<T, K, CLAMP>(p, g, ct, out, r + 1, src, S1, S0, S2, Q1, Q0, Q2, P0, P2, P1);
+        ok = FGML_STEP(r + 1, S1, S0, S2, Q1, Q0, Q2, P0, P2, P1);
         if (!ok || r + 2 > r_end) break;
-        ok = step<T, K, CLAMP>(p, g, ct, out, r + 2, src, S2, S1, S0, Q2, Q1, Q0, P1, P0, P2);
+        ok = FGML_STEP(r + 2, S2, S1, S0, Q2, Q1, Q0, P1, P0, P2);
     }
+#undef FGML_STEP
     if (!ok) {
         if ((threadIdx.x & 31) == 0) atomicExch(&g_device_error, 1);
         src.abort();
