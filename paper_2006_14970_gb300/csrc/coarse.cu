@@ -23,7 +23,9 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs &p);
 
 template <typename T, bool CLAMP>
 __global__ void __launch_bounds__(kThreads, 1) coarse_kernel(const CoarseArgs p) {
+    pdl_enter();
     coarse_body<T, CLAMP>(p);
+    pdl_leave();
 }
 
 // One block per image of a batch; each reads its arguments from the device list.
@@ -163,8 +165,7 @@ cudaError_t launch_t(const CoarseArgs &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(coarse_kernel<T, CLAMP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    coarse_kernel<T, CLAMP><<<1, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(coarse_kernel<T, CLAMP>, dim3(1), dim3(kThreads), smem, s, a);
 }
 
 template <typename T, bool CLAMP>

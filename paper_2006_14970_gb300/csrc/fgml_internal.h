@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cstdint>
+#include <utility>
 
 namespace fgml {
 
@@ -122,6 +123,35 @@ struct CoarseArgs {
 };
 
 enum DType { kF32 = 0, kBF16 = 1, kF16 = 2 };
+
+// Programmatic dependent launch. Kernels of a solve are launched so that the next one
+// may be scheduled while the previous one drains: each kernel first waits for the grids
+// it depends on to finish (and their memory to be visible), before its first global
+// memory access of any kind; a block lets the dependents launch once its work is done.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_leave() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_level_pass(int dtype, int iters, int clamp, const PassArgs &a,

@@ -613,6 +613,7 @@ __device__ __forceinline__ bool run_strip(const PassArgs &p, const LaneGeo &g, c
 
 template <typename T, int K, bool CLAMP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_kernel(const PassArgs p) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (warp >= p.n_warps) return;
@@ -622,11 +623,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_kernel(cons
     lane_setup<T>(p, warp, lane, g, ct, out, K);
     RegSource<T> src;
     run_strip<T, K, CLAMP>(p, g, ct, out, src);
+    pdl_leave();
 }
 
 template <typename T, int K, bool CLAMP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, kRingMinBlocks) level_pass_ring_kernel(const PassArgs p) {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -654,6 +657,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kRingMinBlocks) level_pas
     }
     __syncwarp();
     run_strip<T, K, CLAMP>(p, g, ct, out, src);
+    pdl_leave();
 }
 
 // Tile variant: the warp's rows arrive in chunks of kTileRows rows. A chunk is four
@@ -801,6 +805,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_tile_kernel
     const PassArgs p, const __grid_constant__ CUtensorMap mI, const __grid_constant__ CUtensorMap mA,
     const __grid_constant__ CUtensorMap mF, const __grid_constant__ CUtensorMap mB) {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -843,6 +848,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_tile_kernel
     }
     __syncwarp();
     run_strip<T, K, CLAMP>(p, g, ct, out, src);
+    pdl_leave();
 }
 
 // Work-list batch: one persistent launch runs the level passes of many images. Each
@@ -958,6 +964,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_batch_kernel(
 // Zero sweeps: the level's F and B are the nearest resize of the starting state.
 template <typename T>
 __global__ void resize_fb_kernel(const PassArgs p) {
+    pdl_enter();
     const long long n = (long long)p.w * p.h;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -972,13 +979,13 @@ __global__ void resize_fb_kernel(const PassArgs p) {
             Bd[c] = Bs[c];
         }
     }
+    pdl_leave();
 }
 
 template <typename T, int K, bool CLAMP>
 cudaError_t launch_t(const PassArgs &a, cudaStream_t s) {
     const int blocks = (a.n_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    level_pass_kernel<T, K, CLAMP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(level_pass_kernel<T, K, CLAMP>, dim3(blocks), dim3(kWarpsPerBlock * 32), 0, s, a);
 }
 
 template <typename T, int K, bool CLAMP>
@@ -988,8 +995,7 @@ cudaError_t launch_ring_t(const PassArgs &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(level_pass_ring_kernel<T, K, CLAMP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    level_pass_ring_kernel<T, K, CLAMP><<<blocks, kWarpsPerBlock * 32, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(level_pass_ring_kernel<T, K, CLAMP>, dim3(blocks), dim3(kWarpsPerBlock * 32), smem, s, a);
 }
 
 template <typename T, int K, bool CLAMP, int SLOTS>
@@ -999,8 +1005,8 @@ cudaError_t launch_tile_t(const PassArgs &a, const TileMaps &m, cudaStream_t s) 
     cudaError_t e = cudaFuncSetAttribute(level_pass_tile_kernel<T, K, CLAMP, SLOTS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    level_pass_tile_kernel<T, K, CLAMP, SLOTS><<<blocks, kWarpsPerBlock * 32, smem, s>>>(a, m.I, m.A, m.F, m.B);
-    return cudaGetLastError();
+    return launch_pdl(level_pass_tile_kernel<T, K, CLAMP, SLOTS>, dim3(blocks), dim3(kWarpsPerBlock * 32),
+                      smem, s, a, m.I, m.A, m.F, m.B);
 }
 
 template <typename T, int K, bool CLAMP>
@@ -1021,8 +1027,7 @@ cudaError_t launch_dtype(int iters, int clamp, const PassArgs &a, cudaStream_t s
     if (iters == 0) {
         const long long n = (long long)a.w * a.h;
         const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
-        resize_fb_kernel<T><<<blocks, 256, 0, s>>>(a);
-        return cudaGetLastError();
+        return launch_pdl(resize_fb_kernel<T>, dim3(blocks), dim3(256), 0, s, a);
     }
     if (iters == 1) return clamp ? launch_t<T, 1, true>(a, s) : launch_t<T, 1, false>(a, s);
     return clamp ? launch_t<T, 2, true>(a, s) : launch_t<T, 2, false>(a, s);

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(kThreads) level_small_kernel(const PassArgs p)
     __shared__ float sI[3][RN];
     __shared__ float s0[6][RN];                                       // starting F, B
     __shared__ float s1[6][K == 2 ? W1 * H1 : 1];                     // after sweep 1
+    pdl_enter();
 
     const int tid = threadIdx.x;
     const int X0 = blockIdx.x * kTW, Y0 = blockIdx.y * kTH;
@@ -132,13 +133,13 @@ __global__ void __launch_bounds__(kThreads) level_small_kernel(const PassArgs p)
             st_elem(Bp + c, v[3 + c]);
         }
     }
+    pdl_leave();
 }
 
 template <typename T, int K, bool CLAMP>
 cudaError_t launch_t(const PassArgs &a, cudaStream_t s) {
     const dim3 grid((a.w + kTW - 1) / kTW, (a.h + kTH - 1) / kTH);
-    level_small_kernel<T, K, CLAMP><<<grid, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(level_small_kernel<T, K, CLAMP>, grid, dim3(kThreads), 0, s, a);
 }
 
 template <typename T>

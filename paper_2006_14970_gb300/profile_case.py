@@ -24,9 +24,17 @@ def main():
     ap.add_argument("h", type=int)
     ap.add_argument("--repeat", type=int, default=4)
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--small-iters", type=int, default=None)
+    ap.add_argument("--big-iters", type=int, default=None)
     a = ap.parse_args()
     _build.build()
     from . import fgml, synth
+    kw = {}
+    if a.small_iters is not None:
+        kw["small_iters"] = a.small_iters
+    if a.big_iters is not None:
+        kw["big_iters"] = a.big_iters
+    prm = fgml.params(**kw) if kw else None
     dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
     s = synth.make_sample(a.w, a.h, synth.SEED_BASE + 50)
     I = torch.from_numpy(s.I).cuda().to(dt)
@@ -51,7 +59,7 @@ def main():
         B = torch.empty_like(I)
 
         def run():
-            fgml.estimate(I, A, None, F, B)
+            fgml.estimate(I, A, prm, F, B)
     run()
     start.record()
     for _ in range(max(1, a.repeat - 1)):
@@ -59,7 +67,8 @@ def main():
     stop.record()
     torch.cuda.synchronize()
     ms = start.elapsed_time(stop) / max(1, a.repeat - 1)
-    print(f"{a.case} {a.w}x{a.h} {a.dtype} x{a.repeat}: {ms * 1e3:.1f} us per call "
+    extra = f" {kw}" if kw else ""
+    print(f"{a.case} {a.w}x{a.h} {a.dtype}{extra} x{a.repeat}: {ms * 1e3:.1f} us per call "
           "(back to back, L2 not flushed)")
 
 
