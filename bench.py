@@ -190,7 +190,7 @@ def serving_section(fgml, synth, torch, args):
     out = {"workload": "serving_poisson_256_4096_mixed_f32_bf16",
            "one_at_a_time_f32": {"req_s": cap_req, "mpix_s": cap_px / 1e6}, "rates": []}
     n_req = max(16, args.serving_requests)
-    for x in (0.5, 0.9, 1.2):
+    for x in (0.25, 0.5, 0.75, 0.9, 1.0, 1.2):
         rate = x * cap_req
         gaps = rng.exponential(1.0 / rate, n_req)
         picks = rng.integers(0, len(templates), n_req)
@@ -269,7 +269,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=200)
+    ap.add_argument("--serving-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

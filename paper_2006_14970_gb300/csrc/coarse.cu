@@ -1,11 +1,14 @@
 // Coarse levels: every level of at most 1024 pixels (with the paper's schedule, all
 // the 10-sweep levels up to 32 x 32, Section III-D) runs inside one persistent
-// 1024-thread block, one pixel per thread, from the 1x1 start of Algorithm 1 up to level
-// `nlev`.
+// 1024-thread block, from the 1x1 start of Algorithm 1 up to level `nlev`.
 //  - I_l and alpha_l of every coarse level are gathered from the full-resolution input
-//    (nearest resize, Algorithm 1) in one burst at the start, so HBM latency is paid once.
+//    (nearest resize, Algorithm 1). In float32 the gather is asynchronous (cp.async) in
+//    two groups: the small levels' pixels, which the first sweeps wait for, and the rest,
+//    which arrive while the small levels run.
 //  - F and B live in shared memory as (F, B) pairs per channel, ping-ponged between two
-//    buffers, with one block barrier per Jacobi sweep.
+//    buffers, with one barrier per Jacobi sweep over the warps that hold the level.
+//  - Levels of at most 64 pixels run one thread per (pixel, channel), so a sweep is a
+//    short dependent chain per thread; larger levels run one thread per pixel.
 //  - Each thread forms its pixel's neighbour weights and the inverse of its 2x2 matrix
 //    (Section III-C) once per level; a sweep is then 4 neighbour reads, packed
 //    multiply-adds and the clamped solve (Algorithm 1).
@@ -15,6 +18,7 @@ namespace fgml {
 namespace {
 
 constexpr int kThreads = 1024;
+constexpr int kSplitMax = 64;   // levels up to this many pixels run one thread per (pixel, channel)
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 
@@ -34,76 +38,129 @@ __global__ void __launch_bounds__(kThreads, 1) coarse_batch_kernel(const CoarseA
     coarse_body<T, CLAMP>(list[blockIdx.x]);
 }
 
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// Source pixel of gathered pixel `idx` (levels stored one after another from p.off[0]).
+__device__ __forceinline__ void gather_src(const CoarseArgs &p, int idx, int &gx, int &gy) {
+    int l = 0;
+    while (l + 1 < p.nlev && p.off[l + 1] <= idx) ++l;
+    const int w = p.lw[l], h = p.lh[l], i = idx - p.off[l];
+    const int x = i % w, y = i / w;
+    gx = nearest_src(x, p.Iw, w);
+    gy = nearest_src(y, p.Ih, h);
+}
+
+// Barrier over the first nt threads (a multiple of 32) of the block.
+__device__ __forceinline__ void level_sync(int nt) {
+    if (nt == 32) __syncwarp();
+    else if (nt == kThreads) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" :: "r"(nt) : "memory");
+}
+
 template <typename T, bool CLAMP>
 __device__ __forceinline__ void coarse_body(const CoarseArgs &p) {
     extern __shared__ __align__(16) float sm[];
     // [0, 3 * kCoarseCap) float2: buffer X; then buffer Y; then per level I (3 floats per
     // pixel) and alpha, at the offsets p.off[l] (in pixels)
-    float2 *bufX = reinterpret_cast<float2 *>(sm);
-    float2 *bufY = bufX + 3 * kCoarseCap;
-    float *Ilv = reinterpret_cast<float *>(bufY + 3 * kCoarseCap);
+    float2 *const buf = reinterpret_cast<float2 *>(sm);
+    float *Ilv = reinterpret_cast<float *>(buf + 2 * 3 * kCoarseCap);
     float *Alv = Ilv + 3 * p.total;
     const T *I = static_cast<const T *>(p.I);
     const T *A = static_cast<const T *>(p.A);
     const int tid = threadIdx.x;
 
-    // gather I_l and alpha_l of all coarse levels: every load issued before any store
-    constexpr int kPer = kCoarseTotal / kThreads;
-    float gI[kPer][3], gA[kPer];
+    // pixels of the leading levels that run one thread per (pixel, channel)
+    int split_px = 0;
+    for (int l = 0; l < p.nlev && p.lw[l] * p.lh[l] <= kSplitMax; ++l) split_px = p.off[l] + p.lw[l] * p.lh[l];
+
+    if (sizeof(T) == 4) {
+        // asynchronous gather: group 0 the small levels, group 1 the rest
+        const uint32_t sI = static_cast<uint32_t>(__cvta_generic_to_shared(Ilv));
+        const uint32_t sA = static_cast<uint32_t>(__cvta_generic_to_shared(Alv));
+        for (int g = 0; g < 2; ++g) {
+            const int lo = g == 0 ? 0 : split_px, hi = g == 0 ? split_px : p.total;
+            for (int idx = lo + tid; idx < hi; idx += kThreads) {
+                int gx, gy;
+                gather_src(p, idx, gx, gy);
+                const T *Ip = I + (long long)gy * p.I_pitch + 3 * gx;
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const int idx = tid + k * kThreads;
-        if (idx < p.total) {
-            int l = 0;
-            while (l + 1 < p.nlev && p.off[l + 1] <= idx) ++l;
-            const int w = p.lw[l], h = p.lh[l], i = idx - p.off[l];
-            const int x = i % w, y = i / w;
-            const int gx = nearest_src(x, p.Iw, w), gy = nearest_src(y, p.Ih, h);
-            const T *Ip = I + (long long)gy * p.I_pitch + 3 * gx;
-            gI[k][0] = ld_elem(Ip + 0);
-            gI[k][1] = ld_elem(Ip + 1);
-            gI[k][2] = ld_elem(Ip + 2);
-            gA[k] = ld_elem(A + (long long)gy * p.A_pitch + gx);
+                for (int c = 0; c < 3; ++c) cp_async4(sI + 4u * (3 * idx + c), Ip + c);
+                cp_async4(sA + 4u * idx, A + (long long)gy * p.A_pitch + gx);
+            }
+            cp_async_commit();
+        }
+        cp_async_wait<1>();
+    } else {
+        // 16-bit storage: every load issued before any store
+        constexpr int kPer = kCoarseTotal / kThreads;
+        float gI[kPer][3], gA[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int idx = tid + k * kThreads;
+            if (idx < p.total) {
+                int gx, gy;
+                gather_src(p, idx, gx, gy);
+                const T *Ip = I + (long long)gy * p.I_pitch + 3 * gx;
+                gI[k][0] = ld_elem(Ip + 0);
+                gI[k][1] = ld_elem(Ip + 1);
+                gI[k][2] = ld_elem(Ip + 2);
+                gA[k] = ld_elem(A + (long long)gy * p.A_pitch + gx);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int idx = tid + k * kThreads;
+            if (idx < p.total) {
+                Ilv[3 * idx + 0] = gI[k][0];
+                Ilv[3 * idx + 1] = gI[k][1];
+                Ilv[3 * idx + 2] = gI[k][2];
+                Alv[idx] = gA[k];
+            }
         }
     }
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const int idx = tid + k * kThreads;
-        if (idx < p.total) {
-            Ilv[3 * idx + 0] = gI[k][0];
-            Ilv[3 * idx + 1] = gI[k][1];
-            Ilv[3 * idx + 2] = gI[k][2];
-            Alv[idx] = gA[k];
-        }
-    }
-    float2 *cur = bufX, *nxt = bufY;
+    int cur = 0;   // buffer holding the current state: buf + cur * 3 * kCoarseCap
     if (tid == 0)
-        for (int c = 0; c < 3; ++c) cur[c * kCoarseCap] = f2(p.init, p.init);   // 1 x 1 start
-    __syncthreads();
+        for (int c = 0; c < 3; ++c) buf[c * kCoarseCap] = f2(p.init, p.init);   // 1 x 1 start
 
     int pw = 1, ph = 1;
+    bool rest_waited = false;
     for (int l = 0; l < p.nlev; ++l) {
         const int w = p.lw[l], h = p.lh[l], k = p.lk[l], n = w * h, o = p.off[l];
-        const bool mine = tid < n;
-        const int x = mine ? tid % w : 0, y = mine ? tid / w : 0;
-        // starting F, B: nearest resize of the previous level
-        if (mine) {
-            const int q = nearest_src(y, ph, h) * pw + nearest_src(x, pw, w);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) nxt[c * kCoarseCap + tid] = cur[c * kCoarseCap + q];
+        const bool split = n <= kSplitMax;
+        if (!split && !rest_waited && sizeof(T) == 4) {
+            cp_async_wait<0>();
+            rest_waited = true;
         }
-        // neighbours clamped onto the level (Algorithm 1), their weights and A^{-1}
-        int nb[4] = {0, 0, 0, 0};
-        float wj[4] = {0.f, 0.f, 0.f, 0.f};
-        float ai = 0.f, be = 0.f, mFF = 0.f, mBB = 0.f, nFB = 0.f, Ic[3] = {0.f, 0.f, 0.f};
-        if (mine) {
+        __syncthreads();   // the previous level (and the gathered inputs) are visible
+        const int nact = split ? 3 * n : n;        // active threads
+        const int nt = (nact + 31) & ~31;          // threads taking part in the barriers
+        if (tid < nt) {
+            const bool mine = tid < nact;
+            // split levels: thread = (channel c, pixel i); else thread = pixel i, all channels
+            const int c0 = split && mine ? tid / n : 0;
+            const int i = mine ? tid - c0 * n : 0;
+            const int x = i % w, y = i / w;
+            const int nc = split ? 1 : 3;
+            float2 *src = buf + cur * 3 * kCoarseCap;
+            float2 *dst = buf + (cur ^ 1) * 3 * kCoarseCap;
+            // starting F, B: nearest resize of the previous level
+            if (mine) {
+                const int q = nearest_src(y, ph, h) * pw + nearest_src(x, pw, w);
+                for (int c = c0; c < c0 + nc; ++c) dst[c * kCoarseCap + i] = src[c * kCoarseCap + q];
+            }
+            // neighbours clamped onto the level (Algorithm 1), their weights and A^{-1}
+            int nb[4];
             nb[0] = y * w + max(x - 1, 0);
             nb[1] = y * w + min(x + 1, w - 1);
             nb[2] = max(y - 1, 0) * w + x;
             nb[3] = min(y + 1, h - 1) * w + x;
-            ai = Alv[o + tid];
-            be = 1.f - ai;
-            float S = 0.f;
+            const float ai = Alv[o + i], be = 1.f - ai;
+            float wj[4], S = 0.f;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 wj[j] = fmaf(p.omega, fabsf(ai - Alv[o + nb[j]]), p.eps);
@@ -111,48 +168,73 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs &p) {
             }
             const float A00 = fmaf(ai, ai, S), A11 = fmaf(be, be, S), A01 = ai * be;
             const float m = __fdividef(1.f, fmaf(A00, A11, -A01 * A01));
-            mFF = A11 * m;
-            mBB = A00 * m;
-            nFB = -A01 * m;
+            const float mFF = A11 * m, mBB = A00 * m, nFB = -A01 * m;
+            float Ic[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) Ic[c] = Ilv[3 * (o + tid) + c];
-        }
-        __syncthreads();
-        { float2 *t = cur; cur = nxt; nxt = t; }
+            for (int c = 0; c < 3; ++c) Ic[c] = Ilv[3 * (o + i) + (split ? c0 : c)];
+            cur ^= 1;
+            level_sync(nt);
 
-        for (int it = 0; it < k; ++it) {
-            if (mine) {
+            auto solve = [&](float2 sv, float Icc) {
+                const float bF = fmaf(ai, Icc, sv.x), bB = fmaf(be, Icc, sv.y);
+                float gF = fmaf(mFF, bF, nFB * bB);
+                float gB = fmaf(mBB, bB, nFB * bF);
+                if (CLAMP) {
+                    gF = __saturatef(gF);
+                    gB = __saturatef(gB);
+                }
+                return f2(gF, gB);
+            };
+            if (split) {
+                const int cb = c0 * kCoarseCap;
+                for (int it = 0; it < k; ++it) {
+                    const float2 *s2 = buf + cur * 3 * kCoarseCap + cb;
+                    float2 *d2 = buf + (cur ^ 1) * 3 * kCoarseCap + cb;
+                    if (mine) {
+                        float2 sv = __fmul2_rn(f2(wj[0], wj[0]), s2[nb[0]]);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    // (sum s_j F_j, sum s_j B_j) as one packed pair
-                    float2 s = __fmul2_rn(f2(wj[0], wj[0]), cur[c * kCoarseCap + nb[0]]);
-#pragma unroll
-                    for (int j = 1; j < 4; ++j)
-                        s = __ffma2_rn(f2(wj[j], wj[j]), cur[c * kCoarseCap + nb[j]], s);
-                    const float bF = fmaf(ai, Ic[c], s.x), bB = fmaf(be, Ic[c], s.y);
-                    float gF = fmaf(mFF, bF, nFB * bB);
-                    float gB = fmaf(mBB, bB, nFB * bF);
-                    if (CLAMP) {
-                        gF = __saturatef(gF);
-                        gB = __saturatef(gB);
+                        for (int j = 1; j < 4; ++j) sv = __ffma2_rn(f2(wj[j], wj[j]), s2[nb[j]], sv);
+                        d2[i] = solve(sv, Ic[0]);
                     }
-                    nxt[c * kCoarseCap + tid] = f2(gF, gB);
+                    cur ^= 1;
+                    level_sync(nt);
+                }
+            } else {
+                for (int it = 0; it < k; ++it) {
+                    const float2 *s2 = buf + cur * 3 * kCoarseCap;
+                    float2 *d2 = buf + (cur ^ 1) * 3 * kCoarseCap;
+                    if (mine) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            // (sum s_j F_j, sum s_j B_j) as one packed pair
+                            float2 sv = __fmul2_rn(f2(wj[0], wj[0]), s2[c * kCoarseCap + nb[0]]);
+#pragma unroll
+                            for (int j = 1; j < 4; ++j)
+                                sv = __ffma2_rn(f2(wj[j], wj[j]), s2[c * kCoarseCap + nb[j]], sv);
+                            d2[c * kCoarseCap + i] = solve(sv, Ic[c]);
+                        }
+                    }
+                    cur ^= 1;
+                    level_sync(nt);
                 }
             }
-            __syncthreads();
-            { float2 *t = cur; cur = nxt; nxt = t; }
+        } else {
+            cur ^= (k + 1) & 1;   // the working threads swapped once per resize and sweep
         }
         pw = w;
         ph = h;
     }
+    if (sizeof(T) == 4 && !rest_waited) cp_async_wait<0>();
+    __syncthreads();
 
+    const float2 *fin = buf + cur * 3 * kCoarseCap;
     T *F = static_cast<T *>(p.Fd);
     T *B = static_cast<T *>(p.Bd);
     if (tid < pw * ph) {
         const int x = tid % pw, y = tid / pw;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float2 v = cur[c * kCoarseCap + tid];
+            const float2 v = fin[c * kCoarseCap + tid];
             st_elem(F + (long long)y * p.d_pitch + 3 * x + c, v.x);
             st_elem(B + (long long)y * p.d_pitch + 3 * x + c, v.y);
         }

@@ -42,6 +42,9 @@ constexpr int kLaneCols = 64;        // columns held by a warp (2 per lane)
 constexpr int kWaitPolls = 1 << 20;          // try_wait polls before a wait gives up
 constexpr uint32_t kWaitHintNs = 2000;       // suspend-time hint of one poll
 constexpr int kTileRows = 4;                 // rows per tensor-copy chunk (gather mode: 4)
+#ifndef FGML_TILE_MIN_BLOCKS
+#define FGML_TILE_MIN_BLOCKS 2
+#endif
 #ifndef FGML_RING_MIN_BLOCKS
 #define FGML_RING_MIN_BLOCKS 2
 #endif
@@ -801,7 +804,7 @@ struct TileSource {
 };
 
 template <typename T, int K, bool CLAMP, int SLOTS>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_pass_tile_kernel(
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, FGML_TILE_MIN_BLOCKS) level_pass_tile_kernel(
     const PassArgs p, const __grid_constant__ CUtensorMap mI, const __grid_constant__ CUtensorMap mA,
     const __grid_constant__ CUtensorMap mF, const __grid_constant__ CUtensorMap mB) {
     extern __shared__ __align__(128) unsigned char smem[];
