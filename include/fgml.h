@@ -47,8 +47,19 @@ typedef enum {
 
 typedef enum { FG_F32 = 0, FG_BF16 = 1, FG_F16 = 2 } fg_dtype;
 
-/* Update orders. Jacobi: every pixel of sweep t+1 reads sweep t (the GPU order). */
-typedef enum { FG_ORDER_JACOBI = 0 } fg_order;
+/*
+ * Update orders of the per-pixel solves of one iteration (Algorithm 1 iterates the
+ * closed-form update of Section III-C; the order of the updates inside an iteration is
+ * not fixed by the method's result, only by its convergence).
+ *  FG_ORDER_JACOBI:   every pixel of iteration t+1 reads iteration t (the default).
+ *  FG_ORDER_REDBLACK: an iteration updates the pixels with x + y even, then those with
+ *                     x + y odd, each reading the latest values; a pixel reads only
+ *                     pixels of the other colour (or itself at a clamped border), so the
+ *                     result does not depend on the order inside a colour. Levels run in
+ *                     tiles with a halo of 2 cells per iteration; fg_estimate_batch and
+ *                     the server run red-black image by image.
+ */
+typedef enum { FG_ORDER_JACOBI = 0, FG_ORDER_REDBLACK = 1 } fg_order;
 
 /*
  * Parameters of Algorithm 1. fg_params_default() fills the paper's values:
@@ -62,7 +73,7 @@ typedef struct {
     int small_size;    /* a level is "small" if w_l <= small_size and h_l <= small_size */
     int small_iters;   /* sweeps on small levels, >= 0 */
     int big_iters;     /* sweeps on the other levels, >= 0 */
-    int order;         /* fg_order; only FG_ORDER_JACOBI */
+    int order;         /* fg_order: FG_ORDER_JACOBI or FG_ORDER_REDBLACK */
     int clamp;         /* nonzero: clamp F and B to [0, 1] after each solve */
     float init;        /* value of the 1x1 starting F and B */
 } fg_params;

@@ -101,8 +101,8 @@ fg_status check_params(const fg_params &p) {
         return fail(FG_ERR_INVALID_ARG, "iteration counts and small_size must be >= 0");
     if (p.small_iters > 1000000 || p.big_iters > 1000000)
         return fail(FG_ERR_INVALID_ARG, "iteration counts above 1e6");
-    if (p.order != FG_ORDER_JACOBI)
-        return fail(FG_ERR_UNSUPPORTED, "only the Jacobi order runs on the GPU");
+    if (p.order != FG_ORDER_JACOBI && p.order != FG_ORDER_REDBLACK)
+        return fail(FG_ERR_UNSUPPORTED, "order %d is not available on the GPU (Jacobi or red-black)", p.order);
     if (!std::isfinite(p.init)) return fail(FG_ERR_INVALID_ARG, "init must be finite");
     return FG_OK;
 }
@@ -371,6 +371,8 @@ cudaError_t pass(int dtype, int iters, int clamp, const fg_params &p, const Inpu
     a.n_xstrips = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
     a.n_warps = a.n_xstrips * ((h + a.strip_h - 1) / a.strip_h);
     a.capI = a.capA = a.capS = a.slot_bytes = 0;
+    if (p.order == FG_ORDER_REDBLACK && (iters == 1 || iters == 2))
+        return launch_level_rb(dtype, iters, clamp, a, s);
     if ((iters == 1 || iters == 2) && (long long)w * h <= small_level_pixels())
         return launch_level_small(dtype, iters, clamp, a, s);
     if (iters == 1 || iters == 2) {
@@ -455,6 +457,7 @@ fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
     ca.eps = p.eps_r;
     ca.omega = p.omega;
     ca.init = p.init;
+    ca.order = p.order;
     State src{};
     int buf = -1;
     if (nc == n) {
@@ -870,6 +873,7 @@ extern "C" fg_status fg_estimate_noalloc(const fg_image *I, const fg_image *alph
     ca.eps = p.eps_r;
     ca.omega = p.omega;
     ca.init = p.init;
+    ca.order = p.order;
     State src{};
     int buf = -1;
     if (nc == n) {
@@ -1028,8 +1032,9 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
         m.buf_off = buf_total;
         buf_total += 2 * m.need;
     }
-    if (zero_sweeps) {
-        // levels without sweeps are plain resizes; run such parameter sets image by image
+    if (zero_sweeps || p.order != FG_ORDER_JACOBI) {
+        // levels without sweeps are plain resizes, and the work-list kernel runs the Jacobi
+        // order only; run such parameter sets image by image
         for (int i = 0; i < n; ++i)
             if ((st = estimate(im[i].in, dtype, p, F[i].ptr, B[i].ptr, F[i].row_pitch_bytes / es, s)) != FG_OK)
                 return st;

@@ -12,6 +12,8 @@
 //  - Each thread forms its pixel's neighbour weights and the inverse of its 2x2 matrix
 //    (Section III-C) once per level; a sweep is then 4 neighbour reads, packed
 //    multiply-adds and the clamped solve (Algorithm 1).
+//  - With the red-black order an iteration is two in-place half-sweeps (x + y even, then
+//    odd) over the one current buffer.
 #include "fgml_internal.h"
 
 namespace fgml {
@@ -185,7 +187,31 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs &p) {
                 }
                 return f2(gF, gB);
             };
-            if (split) {
+            if (p.order == 1) {
+                // red-black: per iteration the x + y even pixels, then the odd ones, each
+                // colour in place (it reads only the other colour, or itself at a border)
+                const int cb = split ? c0 * kCoarseCap : 0;
+                const bool on0 = mine && ((x + y) & 1) == 0, on1 = mine && ((x + y) & 1) == 1;
+                float2 *st = buf + cur * 3 * kCoarseCap + cb;
+                for (int it = 0; it < 2 * k; ++it) {
+                    if ((it & 1) ? on1 : on0) {
+                        auto one = [&](int c) {
+                            float2 sv = __fmul2_rn(f2(wj[0], wj[0]), st[c * kCoarseCap + nb[0]]);
+#pragma unroll
+                            for (int j = 1; j < 4; ++j)
+                                sv = __ffma2_rn(f2(wj[j], wj[j]), st[c * kCoarseCap + nb[j]], sv);
+                            st[c * kCoarseCap + i] = solve(sv, Ic[c]);
+                        };
+                        if (split) {
+                            one(0);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) one(c);
+                        }
+                    }
+                    level_sync(nt);
+                }
+            } else if (split) {
                 const int cb = c0 * kCoarseCap;
                 for (int it = 0; it < k; ++it) {
                     const float2 *s2 = buf + cur * 3 * kCoarseCap + cb;
@@ -219,7 +245,8 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs &p) {
                 }
             }
         } else {
-            cur ^= (k + 1) & 1;   // the working threads swapped once per resize and sweep
+            // the working threads swapped once for the resize and (Jacobi) once per sweep
+            cur ^= p.order == 1 ? 1 : (k + 1) & 1;
         }
         pw = w;
         ph = h;

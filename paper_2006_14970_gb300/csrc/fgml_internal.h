@@ -120,6 +120,7 @@ struct CoarseArgs {
     void *Fd, *Bd;                         // F and B of level nlev
     long long d_pitch;
     float eps, omega, init;
+    int order;                             // 0 Jacobi, 1 red-black
 };
 
 enum DType { kF32 = 0, kBF16 = 1, kF16 = 2 };
@@ -167,6 +168,8 @@ cudaError_t launch_level_pass_tile(int dtype, int iters, int clamp, const PassAr
                                    const TileMaps &m, cudaStream_t s);
 size_t level_pass_tile_smem(int chunk_bytes, int slots);
 // Small-level variant: one block per 32 x 16 output tile, all sweeps in shared memory.
+// Red-black order: `iters` (1 or 2) red-black iterations of a level in one launch.
+cudaError_t launch_level_rb(int dtype, int iters, int clamp, const PassArgs &a, cudaStream_t s);
 cudaError_t launch_level_small(int dtype, int iters, int clamp, const PassArgs &a,
                                cudaStream_t s);
 int level_pass_tile_rows();

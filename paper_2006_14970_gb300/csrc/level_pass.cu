@@ -143,14 +143,14 @@ __device__ __forceinline__ void update(const RowK &k, const FB &c, const FB &up,
         const float rF = __shfl_down_sync(kFull, c.F[ch].x, 1);
         const float lB = __shfl_up_sync(kFull, c.B[ch].y, 1);
         const float rB = __shfl_down_sync(kFull, c.B[ch].x, 1);
-        float2 sF = fma2(k.ws, c.F[ch], mul2(k.wu, up.F[ch]));
-        sF = fma2(k.wl, f2(lF, c.F[ch].x), sF);
-        sF = fma2(k.wr, f2(c.F[ch].y, rF), sF);
-        sF = fma2(k.wd, dn.F[ch], sF);
-        float2 sB = fma2(k.ws, c.B[ch], mul2(k.wu, up.B[ch]));
-        sB = fma2(k.wl, f2(lB, c.B[ch].x), sB);
-        sB = fma2(k.wr, f2(c.B[ch].y, rB), sB);
-        sB = fma2(k.wd, dn.B[ch], sB);
+        // vertical and own terms packed over the pixel pair; the horizontal ones, whose
+        // operands straddle lanes, as scalar multiply-adds (no register pairing moves)
+        float2 sF = fma2(k.wd, dn.F[ch], fma2(k.ws, c.F[ch], mul2(k.wu, up.F[ch])));
+        sF.x = fmaf(k.wl.x, lF, fmaf(k.wr.x, c.F[ch].y, sF.x));
+        sF.y = fmaf(k.wl.y, c.F[ch].x, fmaf(k.wr.y, rF, sF.y));
+        float2 sB = fma2(k.wd, dn.B[ch], fma2(k.ws, c.B[ch], mul2(k.wu, up.B[ch])));
+        sB.x = fmaf(k.wl.x, lB, fmaf(k.wr.x, c.B[ch].y, sB.x));
+        sB.y = fmaf(k.wl.y, c.B[ch].x, fmaf(k.wr.y, rB, sB.y));
         const float2 bF = fma2(k.a, k.I[ch], sF);              // alpha I + sum s_j F_j
         const float2 bB = fma2(be, k.I[ch], sB);               // (1-alpha) I + sum s_j B_j
         const float2 tF = mul2(k.nFB, bB);

@@ -17,6 +17,7 @@ from . import build as _build
 FG_OK, FG_ERR_INVALID_ARG, FG_ERR_OOM, FG_ERR_CUDA, FG_ERR_TIMEOUT, FG_ERR_RANGE, \
     FG_ERR_BUSY, FG_ERR_UNSUPPORTED = range(8)
 FG_F32, FG_BF16, FG_F16 = 0, 1, 2
+ORDER_JACOBI, ORDER_REDBLACK = 0, 1
 
 _DTYPES = {torch.float32: FG_F32, torch.bfloat16: FG_BF16, torch.float16: FG_F16}
 
