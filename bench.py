@@ -242,6 +242,32 @@ def serving_section(fgml, synth, torch, args):
     return out
 
 
+def quality_section(fgml, synth, torch, dev, timed):
+    """Error measures of Section IV-C against the generator's known foreground: the
+    2048x1536 workload at the paper's parameters (plus the time of one fg_quality call),
+    and the regularisation sweep of Section IV-F over four 512x384 images with hair."""
+    from paper_2006_14970_gb300 import sweep
+    s = synth.workload(WORKLOAD)
+    I = torch.from_numpy(s.I).to(dev)
+    A = torch.from_numpy(s.alpha).to(dev)
+    Ft = torch.from_numpy(s.F).to(dev)
+    F, _ = fgml.estimate(I, A)
+    at_default = fgml.quality(F, Ft, A)
+    ms = timed(lambda: fgml.quality(F, Ft, A), 5, 3)
+    imgs = []
+    for i in range(4):
+        t = synth.make_sample(512, 384, synth.SEED_BASE + 700 + i, hair=True)
+        imgs.append((torch.from_numpy(t.I).to(dev), torch.from_numpy(t.alpha).to(dev),
+                     torch.from_numpy(t.F).to(dev)))
+    rows = sweep.regularisation_sweep(imgs, [1e-4, 1e-3, 5e-3, 1e-2, 1e-1], [0.0, 0.1, 1.0])
+    best = min(rows, key=lambda r: r["mse"])
+    return {"workload": "single_2048x1536_hair_fp32", "fractional_pixels": int(
+                ((s.alpha > 0) & (s.alpha < 1)).sum()),
+            "at_paper_parameters": at_default, "fg_quality_ms": ms,
+            "sweep": {"images": "4 x 512x384 with hair", "rows": rows,
+                      "min_mse_at": {"eps_r": best["eps_r"], "omega": best["omega"]}}}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -269,6 +295,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -355,7 +382,8 @@ def main():
 
     s, w, h, I, A, F, B = image_case(WORKLOAD)
     levels = fgml.schedule(w, h)
-    n_coarse = sum(1 for (lw, lh, _) in levels if lw * lh <= 4096)
+    # one launch for the levels of at most 1024 pixels, one per level pass after them
+    n_coarse = sum(1 for (lw, lh, _) in levels if lw * lh <= 1024)
     launches_per_step = 1 + (len(levels) - n_coarse)
 
     with Clocks(local) as clk:
@@ -407,6 +435,10 @@ def main():
     if not args.no_serving:
         serving = serving_section(fgml, synth, torch, args)
 
+    quality = None
+    if not args.no_quality:
+        quality = quality_section(fgml, synth, torch, dev, timed)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(WORKLOAD)
@@ -421,7 +453,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "clocks": clocks, "cpu_baseline": cpu, "big": big, "batch": batch,
-                "serving": serving,
+                "serving": serving, "quality": quality,
                 "library": fgml.version()}
         print(json.dumps(line), flush=True)
     if world > 1:

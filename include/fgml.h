@@ -114,6 +114,22 @@ fg_status fg_estimate(const fg_image *I, const fg_image *alpha, const fg_params 
                       fg_image *F, fg_image *B, void *stream);
 
 /*
+ * fg_estimate followed by compositing the foreground onto a new background (Section I,
+ * the compositing equation I = alpha F + (1 - alpha) B, applied with a new background):
+ *   I_new = alpha F + (1 - alpha) B_new   at every pixel,
+ * written by the last level's pass as it stores F, so F is never read back.
+ *  I, alpha, params, F, B: as fg_estimate (F and B are still written).
+ *  B_new: device, w x h x 3, the new background; I_new: device, w x h x 3 output.
+ *  One dtype for all images; the composite is formed in float32 from F's float32
+ *  value (before F itself is rounded to the storage type) and rounded once.
+ *  I_new must not overlap any other image; F and B must not overlap B_new.
+ * Asynchronous on `stream`, like fg_estimate.
+ */
+fg_status fg_estimate_composite(const fg_image *I, const fg_image *alpha, const fg_params *params,
+                                fg_image *F, fg_image *B, const fg_image *B_new, fg_image *I_new,
+                                void *stream);
+
+/*
  * As fg_estimate, but I, alpha, F and B are HOST memory (tightly packed, element type
  * dtype). The library copies the inputs to its device staging buffers, runs the
  * method and copies F and B back, all on `stream`, and returns when F and B are in host
@@ -243,6 +259,22 @@ fg_status fg_server_get_stats(fg_server *s, fg_server_stats *out);
 void fg_server_destroy(fg_server *s);
 /* Message of the calling thread's last server error. */
 const char *fg_server_last_error(void);
+
+/*
+ * Error measures of a foreground estimate against a known foreground (Section IV-C),
+ * over the pixels with 0 < alpha_gt < 1, each weighted by alpha_gt:
+ *   out[0] = SAD  = sum alpha_gt |F_est - F_gt|_1
+ *   out[1] = MSE  = sum alpha_gt |F_est - F_gt|_2^2
+ *   out[2] = GRAD = sum alpha_gt |grad F_est - grad F_gt|_2^2
+ * The norms run over the three channels (and, for GRAD, both gradient components); the
+ * gradient is taken with first-order Gaussian derivative filters of sigma = 1.4 on taps
+ * -6..6 (the Gaussian sampled and normalised to sum 1), image borders repeated.
+ *  F_est, F_gt: device, w x h x 3; alpha_gt: device, w x h; one dtype for all three.
+ *  out: host array of 3 doubles. Sums are per-block doubles added in a fixed order.
+ * Synchronises `stream` (the result is on the host when the call returns).
+ */
+fg_status fg_quality(const fg_image *F_est, const fg_image *F_gt, const fg_image *alpha_gt,
+                     double *out, void *stream);
 
 /* Waits for `stream` and reports any device-side error of the library's kernels. */
 fg_status fg_sync(void *stream);

@@ -188,3 +188,10 @@ def ml(I, alpha, params: Params | None = None):
     if rc != 0:
         raise RuntimeError(f"oracle_ml failed ({rc})")
     return F, B
+
+
+def composite(alpha, F, B_new):
+    """I_new = alpha F + (1 - alpha) B_new per pixel and channel: the compositing equation
+    (Section I) with a new background, in double precision."""
+    a = _f64(alpha)[..., None]
+    return a * _f64(F) + (1.0 - a) * _f64(B_new)

@@ -147,6 +147,7 @@ struct Workspace {
     Buf lev[2];   // intermediate level states: F then B, each w x h x 3
     Buf stage;    // device staging of the host-memory entry point
     Buf batch;    // work lists and per-image levels of fg_estimate_batch
+    Buf aux;      // per-block partial sums of fg_quality
     // launch sequences of fg_estimate captured as CUDA graphs, by call signature
     std::map<std::string, cudaGraphExec_t> graphs;
     std::vector<std::string> graph_order;   // oldest first, for eviction
@@ -345,10 +346,24 @@ bool plan_tile(int dtype, const Input &in, const State &src, PassArgs &a, TileMa
            make_map(&m.B, src.B, inS, src.h, src.pitch * es, a.tile_bwS);
 }
 
+// Compositing epilogue of the last pass of a solve (fg_estimate_composite).
+struct Composite {
+    const void *Bn = nullptr;
+    void *In = nullptr;
+    long long bn_pitch = 0, in_pitch = 0;   // elements
+};
+
 cudaError_t pass(int dtype, int iters, int clamp, const fg_params &p, const Input &in,
                  const State &src, void *Fd, void *Bd, long long d_pitch, int w, int h,
-                 cudaStream_t s) {
+                 cudaStream_t s, const Composite *cmp = nullptr) {
     PassArgs a;
+    std::memset(&a, 0, sizeof a);
+    if (cmp) {
+        a.Bn = cmp->Bn;
+        a.In = cmp->In;
+        a.bn_pitch = cmp->bn_pitch;
+        a.in_pitch = cmp->in_pitch;
+    }
     a.I = in.I;
     a.I_pitch = in.I_pitch;
     a.A = in.A;
@@ -414,11 +429,11 @@ std::vector<int> split_sweeps(int k) {
 // level's final state when it stays in the workspace.
 fg_status run_level(int dtype, const fg_params &p, const Input &in, State &src, int &buf,
                     int k, int w, int h, bool to_caller, void *Fd, void *Bd, long long d_pitch,
-                    Workspace &ws, int es, cudaStream_t s) {
+                    Workspace &ws, int es, cudaStream_t s, const Composite *cmp = nullptr) {
     const std::vector<int> passes = split_sweeps(k);
     for (size_t j = 0; j < passes.size(); ++j) {
         if (to_caller && j + 1 == passes.size()) {
-            cudaError_t e = pass(dtype, passes[j], p.clamp, p, in, src, Fd, Bd, d_pitch, w, h, s);
+            cudaError_t e = pass(dtype, passes[j], p.clamp, p, in, src, Fd, Bd, d_pitch, w, h, s, cmp);
             if (e != cudaSuccess) return cuda_fail(e, "level pass launch");
         } else {
             const int nb = buf == 0 ? 1 : 0;
@@ -436,7 +451,8 @@ fg_status run_level(int dtype, const fg_params &p, const Input &in, State &src, 
 // The kernels of one solve, enqueued on `s` (no allocation, no synchronisation).
 fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
                           const std::vector<Level> &lv, int nc, void *Fd, void *Bd,
-                          long long d_pitch, Workspace &ws, int es, cudaStream_t s) {
+                          long long d_pitch, Workspace &ws, int es, cudaStream_t s,
+                          const Composite *cmp = nullptr) {
     const int n = (int)lv.size();
     CoarseArgs ca;
     std::memset(&ca, 0, sizeof ca);
@@ -464,6 +480,12 @@ fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
         ca.Fd = Fd;
         ca.Bd = Bd;
         ca.d_pitch = d_pitch;
+        if (cmp) {
+            ca.Bn = cmp->Bn;
+            ca.In = cmp->In;
+            ca.bn_pitch = cmp->bn_pitch;
+            ca.in_pitch = cmp->in_pitch;
+        }
     } else {
         src = state_in(ws.lev[0], lv[nc - 1].w, lv[nc - 1].h, es);
         buf = 0;
@@ -476,7 +498,7 @@ fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
 
     for (int l = nc; l < n; ++l) {
         fg_status st = run_level(dtype, p, in, src, buf, lv[l].k, lv[l].w, lv[l].h, l == n - 1,
-                                 Fd, Bd, d_pitch, ws, es, s);
+                                 Fd, Bd, d_pitch, ws, es, s, l == n - 1 ? cmp : nullptr);
         if (st != FG_OK) return st;
     }
     return FG_OK;
@@ -505,7 +527,7 @@ bool graphs_enabled() {
 }
 
 fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, void *Bd,
-                   long long d_pitch, cudaStream_t s) {
+                   long long d_pitch, cudaStream_t s, const Composite *cmp = nullptr) {
     const int es = dtype == kF32 ? 4 : 2;
     const std::vector<Level> lv = plan_levels(in.w, in.h, p);
     const int n = (int)lv.size();
@@ -530,7 +552,7 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
         if (st != FG_OK) return st;
     }
     if (!graphs_enabled())
-        return launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s);
+        return launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp);
 
     // the launch sequence depends on the pointers, pitches, sizes, dtype and parameters
     struct {
@@ -539,6 +561,9 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
         long long Ip, Ap, dp;
         int w, h, dtype;
         fg_params p;
+        const void *Bn;
+        void *In;
+        long long bnp, inp;
     } sig;
     std::memset(&sig, 0, sizeof sig);
     sig.I = in.I;
@@ -552,15 +577,21 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
     sig.h = in.h;
     sig.dtype = dtype;
     sig.p = p;
+    if (cmp) {
+        sig.Bn = cmp->Bn;
+        sig.In = cmp->In;
+        sig.bnp = cmp->bn_pitch;
+        sig.inp = cmp->in_pitch;
+    }
     const std::string key(reinterpret_cast<const char *>(&sig), sizeof sig);
     auto it = ws.graphs.find(key);
     if (it == ws.graphs.end()) {
         cudaStream_t cs = capture_stream();
         if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
-            return launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s);
+            return launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp);
         }
-        fg_status st = launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, cs);
+        fg_status st = launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, cs, cmp);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         if (st != FG_OK) {
@@ -648,6 +679,48 @@ fg_status fg_estimate(const fg_image *I, const fg_image *alpha, const fg_params 
                     (cudaStream_t)stream);
 }
 
+fg_status fg_estimate_composite(const fg_image *I, const fg_image *alpha, const fg_params *params,
+                                fg_image *F, fg_image *B, const fg_image *B_new, fg_image *I_new,
+                                void *stream) {
+    g_err.clear();
+    fg_status st;
+    if ((st = check_image(B_new, 3, "B_new")) != FG_OK) return st;
+    if ((st = check_image(I_new, 3, "I_new")) != FG_OK) return st;
+    if ((st = check_image(I, 3, "I")) != FG_OK) return st;
+    if ((st = check_image(alpha, 1, "alpha")) != FG_OK) return st;
+    if ((st = check_image(F, 3, "F")) != FG_OK) return st;
+    if ((st = check_image(B, 3, "B")) != FG_OK) return st;
+    if (B_new->w != I->w || B_new->h != I->h || I_new->w != I->w || I_new->h != I->h)
+        return fail(FG_ERR_INVALID_ARG, "B_new and I_new must have the size of I");
+    if (B_new->dtype != I->dtype || I_new->dtype != I->dtype)
+        return fail(FG_ERR_INVALID_ARG, "B_new and I_new must have the dtype of I");
+    if (overlap(I_new, 3, I, 3) || overlap(I_new, 3, alpha, 1) || overlap(I_new, 3, F, 3) ||
+        overlap(I_new, 3, B, 3) || overlap(I_new, 3, B_new, 3) || overlap(F, 3, B_new, 3) ||
+        overlap(B, 3, B_new, 3))
+        return fail(FG_ERR_INVALID_ARG, "I_new overlaps another image, or F or B overlaps B_new");
+    const fg_params p = params_or_default(params);
+    if ((st = check_params(p)) != FG_OK) return st;
+    if (alpha->w != I->w || alpha->h != I->h || F->w != I->w || F->h != I->h ||
+        B->w != I->w || B->h != I->h)
+        return fail(FG_ERR_INVALID_ARG, "I, alpha, F and B must have the same size");
+    if (alpha->dtype != I->dtype || F->dtype != I->dtype || B->dtype != I->dtype)
+        return fail(FG_ERR_INVALID_ARG, "I, alpha, F and B must have the same dtype");
+    if (F->row_pitch_bytes != B->row_pitch_bytes)
+        return fail(FG_ERR_INVALID_ARG, "F and B must have the same row pitch");
+    if (overlap(F, 3, B, 3) || overlap(F, 3, I, 3) || overlap(F, 3, alpha, 1) ||
+        overlap(B, 3, I, 3) || overlap(B, 3, alpha, 1))
+        return fail(FG_ERR_INVALID_ARG, "outputs overlap each other or the inputs");
+    const int es = elem_size(I->dtype);
+    Input in{I->ptr, alpha->ptr, I->row_pitch_bytes / es, alpha->row_pitch_bytes / es, I->w, I->h};
+    Composite c;
+    c.Bn = B_new->ptr;
+    c.In = I_new->ptr;
+    c.bn_pitch = B_new->row_pitch_bytes / es;
+    c.in_pitch = I_new->row_pitch_bytes / es;
+    return estimate(in, (int)I->dtype, p, F->ptr, B->ptr, F->row_pitch_bytes / es,
+                    (cudaStream_t)stream, &c);
+}
+
 fg_status fg_estimate_host(const void *I, const void *alpha, int w, int h, fg_dtype dtype,
                            const fg_params *params, void *F, void *B, void *stream) {
     g_err.clear();
@@ -725,6 +798,54 @@ fg_status fg_level_pass(const fg_image *I, const fg_image *alpha, const fg_image
                      F_dst->row_pitch_bytes / es, ws, es, s);
 }
 
+fg_status fg_quality(const fg_image *F_est, const fg_image *F_gt, const fg_image *alpha_gt,
+                     double *out, void *stream) {
+    g_err.clear();
+    fg_status st;
+    if ((st = check_image(F_est, 3, "F_est")) != FG_OK) return st;
+    if ((st = check_image(F_gt, 3, "F_gt")) != FG_OK) return st;
+    if ((st = check_image(alpha_gt, 1, "alpha_gt")) != FG_OK) return st;
+    if (!out) return fail(FG_ERR_INVALID_ARG, "out is NULL");
+    if (F_gt->w != F_est->w || F_gt->h != F_est->h || alpha_gt->w != F_est->w || alpha_gt->h != F_est->h)
+        return fail(FG_ERR_INVALID_ARG, "F_est, F_gt and alpha_gt must have the same size");
+    const fg_dtype dt = F_est->dtype;
+    if (F_gt->dtype != dt || alpha_gt->dtype != dt)
+        return fail(FG_ERR_INVALID_ARG, "F_est, F_gt and alpha_gt must have the same dtype");
+    const int es = elem_size(dt);
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace &ws = workspace_for(s);
+    const long long nb = quality_blocks(F_est->w, F_est->h);
+    if ((st = ensure(ws.aux, (size_t)(3 * nb + 3) * sizeof(double), s)) != FG_OK) return st;
+    QualityArgs q;
+    std::memset(&q, 0, sizeof q);
+    q.Fe = F_est->ptr;
+    q.Fg = F_gt->ptr;
+    q.A = alpha_gt->ptr;
+    q.fe_pitch = F_est->row_pitch_bytes / es;
+    q.fg_pitch = F_gt->row_pitch_bytes / es;
+    q.a_pitch = alpha_gt->row_pitch_bytes / es;
+    q.w = F_est->w;
+    q.h = F_est->h;
+    // sampled Gaussian (normalised to sum 1) and its derivative, sigma = 1.4 (Section IV-C)
+    const double sigma = 1.4;
+    double g[2 * kQualityRadius + 1], sum = 0.0;
+    for (int k = -kQualityRadius; k <= kQualityRadius; ++k)
+        sum += g[k + kQualityRadius] = std::exp(-0.5 * k * k / (sigma * sigma));
+    for (int k = -kQualityRadius; k <= kQualityRadius; ++k) {
+        const double gk = g[k + kQualityRadius] / sum;
+        q.g[k + kQualityRadius] = (float)gk;
+        q.dg[k + kQualityRadius] = (float)(-k / (sigma * sigma) * gk);
+    }
+    q.partials = static_cast<double *>(ws.aux.p);
+    double *dout = q.partials + 3 * nb;
+    cudaError_t e = launch_quality((int)dt, q, dout, s);
+    if (e != cudaSuccess) return cuda_fail(e, "quality kernel launch");
+    e = cudaMemcpyAsync(out, dout, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "quality result copy");
+    return FG_OK;
+}
+
 fg_status fg_sync(void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
@@ -751,6 +872,7 @@ fg_status fg_release_workspace(void *stream) {
     cudaFree(w.lev[1].p);
     cudaFree(w.stage.p);
     cudaFree(w.batch.p);
+    cudaFree(w.aux.p);
     return FG_OK;
 }
 

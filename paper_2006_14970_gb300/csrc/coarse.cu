@@ -259,12 +259,17 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs &p) {
     T *B = static_cast<T *>(p.Bd);
     if (tid < pw * ph) {
         const int x = tid % pw, y = tid / pw;
+        float Fv[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const float2 v = fin[c * kCoarseCap + tid];
+            Fv[c] = v.x;
             st_elem(F + (long long)y * p.d_pitch + 3 * x + c, v.x);
             st_elem(B + (long long)y * p.d_pitch + 3 * x + c, v.y);
         }
+        if (p.In)
+            composite_px<T>(p.Bn, p.bn_pitch, p.In, p.in_pitch, x, y,
+                            Alv[p.off[p.nlev - 1] + tid], Fv);
     }
 }
 

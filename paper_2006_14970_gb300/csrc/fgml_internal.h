@@ -61,7 +61,23 @@ struct PassArgs {
     // tile variant only: box widths (8-byte elements), chunk layout (bytes), chunks in flight
     int tile_bwI, tile_bwA, tile_bwS, tile_slots;
     int tile_offA, tile_offF, tile_offB, tile_chunk, tile_tx;
+    // optional compositing epilogue (In == nullptr: none): as the pass stores F it also
+    // writes In = alpha F + (1 - alpha) Bn at the same pixel, alpha being the level's
+    const void *Bn;         // new background, w x h x 3
+    void *In;               // composite, w x h x 3
+    long long bn_pitch, in_pitch;   // elements per row
 };
+
+// Compositing epilogue of one pixel (see PassArgs::In), channels c = 0..2 of F.
+template <typename T>
+__device__ __forceinline__ void composite_px(const void *Bn, long long bn_pitch, void *In,
+                                             long long in_pitch, int x, int y, float a,
+                                             const float *F) {
+    const T *b = static_cast<const T *>(Bn) + (long long)y * bn_pitch + 3 * x;
+    T *o = static_cast<T *>(In) + (long long)y * in_pitch + 3 * x;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) st_elem(o + c, fmaf(a, F[c], (1.f - a) * ld_elem(b + c)));
+}
 
 // One level pass of a work-list batch.
 struct BatchDesc {
@@ -121,9 +137,27 @@ struct CoarseArgs {
     long long d_pitch;
     float eps, omega, init;
     int order;                             // 0 Jacobi, 1 red-black
+    const void *Bn;                        // compositing epilogue of level nlev, as PassArgs
+    void *In;
+    long long bn_pitch, in_pitch;
 };
 
 enum DType { kF32 = 0, kBF16 = 1, kF16 = 2 };
+
+// Error measures (Section IV-C): Gaussian derivative filters of sigma = 1.4 on taps
+// k = -kQualityRadius..kQualityRadius.
+constexpr int kQualityRadius = 6;
+struct QualityArgs {
+    const void *Fe, *Fg, *A;                   // estimate, ground truth (w x h x 3), alpha_gt
+    long long fe_pitch, fg_pitch, a_pitch;     // elements
+    int w, h;
+    float g[2 * kQualityRadius + 1];           // smoothing taps
+    float dg[2 * kQualityRadius + 1];          // derivative taps
+    double *partials;                          // 3 per block (quality_blocks)
+};
+long long quality_blocks(int w, int h);
+// SAD, MSE and GRAD into out[0..2] (device), via per-block partials.
+cudaError_t launch_quality(int dtype, const QualityArgs &q, double *out, cudaStream_t s);
 
 // Programmatic dependent launch. Kernels of a solve are launched so that the next one
 // may be scheduled while the previous one drains: each kernel first waits for the grids

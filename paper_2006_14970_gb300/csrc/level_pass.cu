@@ -170,10 +170,26 @@ struct Out {
     unsigned char *F, *B;
     long long pitch;        // bytes
     bool o0, o1;            // this lane writes p0 / p1
+    const unsigned char *Bn;   // compositing epilogue (In == nullptr: none), same columns
+    unsigned char *In;
+    long long bn_pitch, in_pitch;   // bytes
 };
 
+// Compositing epilogue of a lane's pixel pair in row r: In = alpha F + (1 - alpha) Bn.
 template <typename T>
-__device__ __forceinline__ void store_row(const Out &o, int r, const FB &v) {
+__device__ __forceinline__ void composite_row(const Out &o, int r, const FB &v, float2 a) {
+    const T *Nr = reinterpret_cast<const T *>(o.Bn + (long long)r * o.bn_pitch);
+    T *Cr = reinterpret_cast<T *>(o.In + (long long)r * o.in_pitch);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (o.o0) st_elem(Cr + c, fmaf(a.x, v.F[c].x, (1.f - a.x) * ld_elem(Nr + c)));
+        if (o.o1) st_elem(Cr + 3 + c, fmaf(a.y, v.F[c].y, (1.f - a.y) * ld_elem(Nr + 3 + c)));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_row(const Out &o, int r, const FB &v, float2 a) {
+    if (o.In) composite_row<T>(o, r, v, a);
     T *Fr = reinterpret_cast<T *>(o.F + (long long)r * o.pitch);
     T *Br = reinterpret_cast<T *>(o.B + (long long)r * o.pitch);
     if (sizeof(T) == 4 && o.o0 && o.o1 &&
@@ -517,7 +533,7 @@ __device__ __forceinline__ bool step(const PassArgs &p, const LaneGeo &g, const 
         if (STEADY || (q >= ct.Y0 && q < ct.Y1)) {
             FB res;
             update<CLAMP>(Sr1, Qr1, Qr2, Qr, res);
-            store_row<T>(out, q, res);
+            store_row<T>(out, q, res, Sr1.a);
         }
     } else {
         if (STEADY || (q >= ct.t1_lo && q <= ct.t1_hi)) update<CLAMP>(Sr1, Qr1, Qr2, Qr, Pw);
@@ -525,7 +541,7 @@ __device__ __forceinline__ bool step(const PassArgs &p, const LaneGeo &g, const 
         if (STEADY || (q2 >= ct.Y0 && q2 < ct.Y1)) {
             FB res;
             update<CLAMP>(Sr2, Pr2, Pr3, Pw, res);
-            store_row<T>(out, q2, res);
+            store_row<T>(out, q2, res, Sr2.a);
         }
     }
     return true;
@@ -580,6 +596,10 @@ __device__ __forceinline__ void lane_setup(const PassArgs &p, int warp, int lane
     out.F = static_cast<unsigned char *>(p.Fd) + col;
     out.B = static_cast<unsigned char *>(p.Bd) + col;
     out.pitch = p.d_pitch * (long long)sizeof(T);
+    out.In = p.In ? static_cast<unsigned char *>(p.In) + col : nullptr;
+    out.Bn = p.In ? static_cast<const unsigned char *>(p.Bn) + col : nullptr;
+    out.bn_pitch = p.bn_pitch * (long long)sizeof(T);
+    out.in_pitch = p.in_pitch * (long long)sizeof(T);
 }
 
 template <typename T, int K, bool CLAMP, typename Src>
@@ -980,6 +1000,12 @@ __global__ void resize_fb_kernel(const PassArgs p) {
         for (int c = 0; c < 3; ++c) {
             Fd[c] = Fs[c];
             Bd[c] = Bs[c];
+        }
+        if (p.In) {
+            const float F[3] = {to_f(Fs[0]), to_f(Fs[1]), to_f(Fs[2])};
+            const int gx = nearest_src(x, p.Iw, p.w), gy = nearest_src(y, p.Ih, p.h);
+            const float a = ld_elem(static_cast<const T *>(p.A) + (long long)gy * p.A_pitch + gx);
+            composite_px<T>(p.Bn, p.bn_pitch, p.In, p.in_pitch, x, y, a, F);
         }
     }
     pdl_leave();

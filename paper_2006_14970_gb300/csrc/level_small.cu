@@ -132,6 +132,9 @@ __global__ void __launch_bounds__(kThreads) level_small_kernel(const PassArgs p)
             st_elem(Fp + c, v[c]);
             st_elem(Bp + c, v[3 + c]);
         }
+        if (p.In)
+            composite_px<T>(p.Bn, p.bn_pitch, p.In, p.in_pitch, x, y,
+                            sA[(y - RY) * RW + (x - RX)], v);
     }
     pdl_leave();
 }

@@ -131,6 +131,10 @@ __global__ void __launch_bounds__(kThreads) level_rb_kernel(const PassArgs p) {
             st_elem(Fp + c, sS[c][i]);
             st_elem(Bp + c, sS[3 + c][i]);
         }
+        if (p.In) {
+            const float F[3] = {sS[0][i], sS[1][i], sS[2][i]};
+            composite_px<T>(p.Bn, p.bn_pitch, p.In, p.in_pitch, x, y, sA[i], F);
+        }
     }
     pdl_leave();
 }

@@ -81,6 +81,11 @@ def load():
     lib.fg_selftest_bounded_wait.restype = ctypes.c_int
     lib.fg_sync.argtypes = [vp]
     lib.fg_sync.restype = ctypes.c_int
+    lib.fg_estimate_composite.argtypes = [P(Image), P(Image), P(Params), P(Image), P(Image),
+                                          P(Image), P(Image), vp]
+    lib.fg_estimate_composite.restype = ctypes.c_int
+    lib.fg_quality.argtypes = [P(Image), P(Image), P(Image), P(ctypes.c_double), vp]
+    lib.fg_quality.restype = ctypes.c_int
     lib.fg_release_workspace.argtypes = [vp]
     lib.fg_release_workspace.restype = ctypes.c_int
     lib.fg_last_error.argtypes = []
@@ -224,6 +229,31 @@ def selftest_bounded_wait(stream=None) -> int:
 
 def sync(stream=None):
     _check(load().fg_sync(_stream(stream)))
+
+
+def estimate_composite(I, alpha, B_new, p: Params | None = None, F=None, B=None, I_new=None,
+                       stream=None):
+    """fg_estimate_composite: (F, B, I_new) with I_new = alpha F + (1 - alpha) B_new
+    formed by the last level's pass."""
+    F = torch.empty_like(I) if F is None else F
+    B = torch.empty_like(I) if B is None else B
+    I_new = torch.empty_like(I) if I_new is None else I_new
+    imgs = [_image(I, 3, "I"), _image(alpha, 1, "alpha"), _image(F, 3, "F"), _image(B, 3, "B"),
+            _image(B_new, 3, "B_new"), _image(I_new, 3, "I_new")]
+    _check(load().fg_estimate_composite(
+        ctypes.byref(imgs[0]), ctypes.byref(imgs[1]), ctypes.byref(p) if p is not None else None,
+        ctypes.byref(imgs[2]), ctypes.byref(imgs[3]), ctypes.byref(imgs[4]), ctypes.byref(imgs[5]),
+        _stream(stream)))
+    return F, B, I_new
+
+
+def quality(F_est, F_gt, alpha_gt, stream=None) -> dict:
+    """fg_quality: SAD, MSE and GRAD of F_est against F_gt over 0 < alpha_gt < 1
+    (Section IV-C); device tensors of one dtype. Synchronises the stream."""
+    out = (ctypes.c_double * 3)()
+    imgs = [_image(F_est, 3, "F_est"), _image(F_gt, 3, "F_gt"), _image(alpha_gt, 1, "alpha_gt")]
+    _check(load().fg_quality(*(ctypes.byref(x) for x in imgs), out, _stream(stream)))
+    return {"sad": out[0], "mse": out[1], "grad": out[2]}
 
 
 def release_workspace(stream=None):

@@ -352,3 +352,15 @@ def test_compositing_residual_small_on_synthetic_matte():
     res = np.abs(a3 * F + (1 - a3) * B - s.I)
     frac = (s.alpha > 0) & (s.alpha < 1)
     assert res[frac].mean() < 0.02
+
+
+def test_composite_closed_forms():
+    # alpha = 1 keeps the foreground, alpha = 0 the new background, and a hand-evaluated
+    # fractional pixel
+    F = np.array([[[0.2, 0.4, 0.6], [0.9, 0.1, 0.5], [1.0, 0.0, 0.25]]])
+    Bn = np.array([[[0.7, 0.3, 0.1], [0.0, 1.0, 0.5], [0.5, 0.5, 0.75]]])
+    a = np.array([[1.0, 0.0, 0.25]])
+    out = oracle.composite(a, F, Bn)
+    assert np.array_equal(out[0, 0], F[0, 0]) and np.array_equal(out[0, 1], Bn[0, 1])
+    assert np.allclose(out[0, 2], [0.25 * 1.0 + 0.75 * 0.5, 0.75 * 0.5, 0.25 * 0.25 + 0.75 * 0.75],
+                       atol=1e-16)
