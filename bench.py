@@ -268,6 +268,30 @@ def quality_section(fgml, synth, torch, dev, timed):
                       "min_mse_at": {"eps_r": best["eps_r"], "omega": best["omega"]}}}
 
 
+def converged_section(fgml, synth, torch, dev):
+    """Distance of the method's output from the minimiser of the global cost (float64
+    conjugate gradients, warm-started from the method's output, to a relative residual of
+    1e-10) on the 2048x1536 workload. The minimiser is unclamped; the method clamps."""
+    s = synth.workload(WORKLOAD)
+    I = torch.from_numpy(s.I).to(dev)
+    A = torch.from_numpy(s.alpha).to(dev)
+    F, B = fgml.estimate(I, A)
+    t0 = time.perf_counter()
+    Fm, Bm, it, rel = fgml.minimiser_cg(I, A, None, F, B, max_iters=20000, rel_tol=1e-10)
+    secs = time.perf_counter() - t0
+    frac = torch.from_numpy((s.alpha > 0) & (s.alpha < 1)).to(dev)
+    dF = (F.double() - Fm).abs()
+    dB = (B.double() - Bm).abs()
+    inside = ((Fm >= 0) & (Fm <= 1)).all(dim=-1) & frac
+    return {"workload": "single_2048x1536_hair_fp32", "cg_iterations": it,
+            "cg_relative_residual": rel, "cg_seconds": secs,
+            "F_max_abs": float(dF.max()), "F_rms": float(dF.pow(2).mean().sqrt()),
+            "B_max_abs": float(dB.max()), "B_rms": float(dB.pow(2).mean().sqrt()),
+            "F_rms_fractional": float(dF[frac].pow(2).mean().sqrt()),
+            "F_max_abs_fractional_minimiser_in_unit_box": float(dF[inside].max())
+            if bool(inside.any()) else None}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -296,6 +320,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -439,6 +464,10 @@ def main():
     if not args.no_quality:
         quality = quality_section(fgml, synth, torch, dev, timed)
 
+    converged = None
+    if not args.no_cg:
+        converged = converged_section(fgml, synth, torch, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(WORKLOAD)
@@ -453,7 +482,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "clocks": clocks, "cpu_baseline": cpu, "big": big, "batch": batch,
-                "serving": serving, "quality": quality,
+                "serving": serving, "quality": quality, "converged_reference": converged,
                 "library": fgml.version()}
         print(json.dumps(line), flush=True)
     if world > 1:

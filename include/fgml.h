@@ -261,6 +261,28 @@ void fg_server_destroy(fg_server *s);
 const char *fg_server_last_error(void);
 
 /*
+ * Converged reference (not part of the method): the minimiser of the global cost whose
+ * per-pixel minimisation Algorithm 1 iterates, at full resolution and without the clamp.
+ * Summing the local cost of Section III-C over the pixels, each 4-neighbour edge once:
+ *   E = sum_i sum_c (alpha_i F_i + (1 - alpha_i) B_i - I_i)^2
+ *     + sum_{edges {i,j}} (eps_r + omega |alpha_i - alpha_j|) sum_c [(F_i - F_j)^2 + (B_i - B_j)^2],
+ * whose stationary point is the fixed point of the unclamped update. Solved by conjugate
+ * gradients on grad E = 0 in float64, preconditioned by the inverse of each pixel's 2x2
+ * diagonal block; E is strictly convex (a unique minimiser) when alpha is not constant.
+ *  I, alpha: device images (one dtype); params: eps_r and omega are used.
+ *  F, B: device float64 arrays of h x w x 3, tightly packed: the starting point on entry
+ *        (zeros, or the method's output converted), the solution on return.
+ *  Stops when |b - H x| <= rel_tol |b| (b = (alpha I, (1 - alpha) I)) or after max_iters
+ *  iterations (checked every 32). *iters (may be NULL): iterations run;
+ *  *rel_residual (may be NULL): |b - H x| / |b| recomputed from the returned x.
+ * Synchronous on `stream`. Workspace: 36 doubles per pixel.
+ * Errors: FG_ERR_RANGE if the iteration diverges (constant alpha).
+ */
+fg_status fg_minimiser_cg(const fg_image *I, const fg_image *alpha, const fg_params *params,
+                          double *F, double *B, int max_iters, double rel_tol, int *iters,
+                          double *rel_residual, void *stream);
+
+/*
  * Error measures of a foreground estimate against a known foreground (Section IV-C),
  * over the pixels with 0 < alpha_gt < 1, each weighted by alpha_gt:
  *   out[0] = SAD  = sum alpha_gt |F_est - F_gt|_1

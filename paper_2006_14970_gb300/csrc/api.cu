@@ -138,6 +138,8 @@ bool overlap(const fg_image *a, int ca, const fg_image *b, int cb) {
 
 // ------------------------------------------------------------------ workspaces
 
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
 struct Buf {
     void *p = nullptr;
     size_t bytes = 0;
@@ -148,6 +150,7 @@ struct Workspace {
     Buf stage;    // device staging of the host-memory entry point
     Buf batch;    // work lists and per-image levels of fg_estimate_batch
     Buf aux;      // per-block partial sums of fg_quality
+    Buf cg;       // vectors of fg_minimiser_cg
     // launch sequences of fg_estimate captured as CUDA graphs, by call signature
     std::map<std::string, cudaGraphExec_t> graphs;
     std::vector<std::string> graph_order;   // oldest first, for eviction
@@ -846,6 +849,82 @@ fg_status fg_quality(const fg_image *F_est, const fg_image *F_gt, const fg_image
     return FG_OK;
 }
 
+fg_status fg_minimiser_cg(const fg_image *I, const fg_image *alpha, const fg_params *params,
+                          double *F, double *B, int max_iters, double rel_tol, int *iters,
+                          double *rel_residual, void *stream) {
+    g_err.clear();
+    fg_status st;
+    if ((st = check_image(I, 3, "I")) != FG_OK) return st;
+    if ((st = check_image(alpha, 1, "alpha")) != FG_OK) return st;
+    if (alpha->w != I->w || alpha->h != I->h || alpha->dtype != I->dtype)
+        return fail(FG_ERR_INVALID_ARG, "I and alpha must have the same size and dtype");
+    if (!F || !B) return fail(FG_ERR_INVALID_ARG, "F or B is NULL");
+    if (max_iters < 0 || !(rel_tol >= 0.0))
+        return fail(FG_ERR_INVALID_ARG, "max_iters must be >= 0 and rel_tol >= 0");
+    const fg_params p = params_or_default(params);
+    if ((st = check_params(p)) != FG_OK) return st;
+    const int es = elem_size(I->dtype), w = I->w, h = I->h;
+    const long long n = (long long)w * h;
+    const size_t vec = (size_t)(6 * n) * sizeof(double);
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace &ws = workspace_for(s);
+    const int nb = cg_blocks(w, h);
+    const size_t vec_al = align256(vec);
+    const size_t need = 6 * vec_al + align256((size_t)3 * nb * sizeof(double)) + sizeof(CgScalars);
+    if ((st = ensure(ws.cg, need, s)) != FG_OK) return st;
+    char *base = static_cast<char *>(ws.cg.p);
+    CgArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.I = I->ptr;
+    a.A = alpha->ptr;
+    a.I_pitch = I->row_pitch_bytes / es;
+    a.A_pitch = alpha->row_pitch_bytes / es;
+    a.w = w;
+    a.h = h;
+    a.eps = p.eps_r;
+    a.omega = p.omega;
+    a.x = reinterpret_cast<double *>(base);
+    a.r = reinterpret_cast<double *>(base + vec_al);
+    a.z = reinterpret_cast<double *>(base + 2 * vec_al);
+    a.q = reinterpret_cast<double *>(base + 3 * vec_al);
+    double *pv[2] = {reinterpret_cast<double *>(base + 4 * vec_al),
+                     reinterpret_cast<double *>(base + 5 * vec_al)};
+    a.partials = reinterpret_cast<double *>(base + 6 * vec_al);
+    a.sc = reinterpret_cast<CgScalars *>(base + 6 * vec_al + align256((size_t)3 * nb * sizeof(double)));
+    const size_t half = vec / 2;
+    cudaError_t e = cudaMemcpyAsync(a.x, F, half, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(a.x + 3 * n, B, half, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cg_start((int)I->dtype, a, pv[0], s);
+    CgScalars hs;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, a.sc, sizeof hs, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "conjugate gradients start");
+    int it = 0, cur = 0;
+    const double stop = rel_tol * rel_tol * hs.bb;
+    while (it < max_iters && hs.rr > stop) {
+        const int chunk = std::min(32, max_iters - it);
+        for (int k = 0; k < chunk && e == cudaSuccess; ++k) {
+            e = cg_iterate((int)I->dtype, a, pv[cur], pv[cur ^ 1], s);
+            cur ^= 1;
+        }
+        it += chunk;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, a.sc, sizeof hs, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "conjugate gradients iteration");
+        if (!std::isfinite(hs.rr)) return fail(FG_ERR_RANGE, "conjugate gradients diverged (is alpha constant?)");
+    }
+    // the reported residual is recomputed from x, not the recursively updated one
+    e = cg_true_residual((int)I->dtype, a, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(F, a.x, half, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B, a.x + 3 * n, half, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, a.sc, sizeof hs, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "conjugate gradients result");
+    if (iters) *iters = it;
+    if (rel_residual) *rel_residual = hs.bb > 0.0 ? std::sqrt(hs.rr / hs.bb) : std::sqrt(hs.rr);
+    return FG_OK;
+}
+
 fg_status fg_sync(void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
@@ -873,6 +952,7 @@ fg_status fg_release_workspace(void *stream) {
     cudaFree(w.stage.p);
     cudaFree(w.batch.p);
     cudaFree(w.aux.p);
+    cudaFree(w.cg.p);
     return FG_OK;
 }
 
@@ -1034,7 +1114,6 @@ int batch_strip_rows(int w, int h) {
     return (int)std::min<long long>(std::max<long long>(r, 8), 64);
 }
 
-size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 PassArgs batch_pass_args(int dtype, const fg_params &p, const Input &in, const State &src,
                          void *Fd, void *Bd, long long d_pitch, int w, int h, bool *ring) {

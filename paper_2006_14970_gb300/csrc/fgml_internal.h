@@ -156,6 +156,46 @@ struct QualityArgs {
     double *partials;                          // 3 per block (quality_blocks)
 };
 long long quality_blocks(int w, int h);
+
+// Sum of one double per thread over the block (blockDim.x a multiple of 32, at most
+// 1024); `red` holds blockDim.x / 32 doubles. The result is valid in thread 0, and the
+// order of the additions is fixed.
+__device__ __forceinline__ double block_sum_d(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    v = 0.0;
+    if (threadIdx.x < nw) v = red[threadIdx.x];
+    if (warp == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Converged reference (fg_minimiser_cg): preconditioned conjugate gradients in float64
+// on grad E = 0. Vectors hold 6 n doubles: F (n x 3, row-major pixels) then B.
+struct CgScalars {
+    double rz, pq, alpha, beta, rr, bb;
+};
+struct CgArgs {
+    const void *I, *A;
+    long long I_pitch, A_pitch;   // elements
+    int w, h;
+    double eps, omega;
+    double *x, *r, *z, *q;
+    double *partials;             // 3 per block
+    CgScalars *sc;                // device
+};
+int cg_blocks(int w, int h);
+// r = b - H x, z = M^-1 r, p = z; rz, bb, rr; beta = 0.
+cudaError_t cg_start(int dtype, const CgArgs &a, double *p, cudaStream_t s);
+// One iteration: p_new = z + beta p_old, q = H p_new, alpha = rz / <p, q>, x += alpha p,
+// r -= alpha q, z = M^-1 r, beta = <r, z> / rz, rr = <r, r>.
+cudaError_t cg_iterate(int dtype, const CgArgs &a, const double *p_old, double *p_new,
+                       cudaStream_t s);
+// rr = |b - H x|^2 recomputed from x (into a.r, a.z used as scratch).
+cudaError_t cg_true_residual(int dtype, const CgArgs &a, cudaStream_t s);
 // SAD, MSE and GRAD into out[0..2] (device), via per-block partials.
 cudaError_t launch_quality(int dtype, const QualityArgs &q, double *out, cudaStream_t s);
 

@@ -20,18 +20,7 @@ constexpr int kTW = 32, kTH = 16, kThreads = 256;
 constexpr int R = kQualityRadius;
 constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R;
 
-__device__ __forceinline__ double block_sum(double v, double *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    v = 0.0;
-    if (threadIdx.x < kThreads / 32) v = red[threadIdx.x];
-    if (warp == 0)
-        for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;   // valid in thread 0
-}
+__device__ __forceinline__ double block_sum(double v, double *red) { return block_sum_d(v, red); }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) quality_kernel(const QualityArgs q) {

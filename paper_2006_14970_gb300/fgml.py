@@ -84,6 +84,9 @@ def load():
     lib.fg_estimate_composite.argtypes = [P(Image), P(Image), P(Params), P(Image), P(Image),
                                           P(Image), P(Image), vp]
     lib.fg_estimate_composite.restype = ctypes.c_int
+    lib.fg_minimiser_cg.argtypes = [P(Image), P(Image), P(Params), vp, vp, ctypes.c_int,
+                                     ctypes.c_double, P(ctypes.c_int), P(ctypes.c_double), vp]
+    lib.fg_minimiser_cg.restype = ctypes.c_int
     lib.fg_quality.argtypes = [P(Image), P(Image), P(Image), P(ctypes.c_double), vp]
     lib.fg_quality.restype = ctypes.c_int
     lib.fg_release_workspace.argtypes = [vp]
@@ -245,6 +248,27 @@ def estimate_composite(I, alpha, B_new, p: Params | None = None, F=None, B=None,
         ctypes.byref(imgs[2]), ctypes.byref(imgs[3]), ctypes.byref(imgs[4]), ctypes.byref(imgs[5]),
         _stream(stream)))
     return F, B, I_new
+
+
+def minimiser_cg(I, alpha, p: Params | None = None, F0=None, B0=None, max_iters: int = 20000,
+                 rel_tol: float = 1e-10, stream=None):
+    """fg_minimiser_cg: the unclamped minimiser of the global cost by float64 conjugate
+    gradients, from (F0, B0) (zeros if None). Returns (F, B, iterations, relative
+    residual); F and B are float64 [H, W, 3] device tensors."""
+    h, w = alpha.shape[0], alpha.shape[1]
+    F = torch.zeros((h, w, 3), dtype=torch.float64, device=I.device) if F0 is None else \
+        F0.to(torch.float64).contiguous().clone()
+    B = torch.zeros((h, w, 3), dtype=torch.float64, device=I.device) if B0 is None else \
+        B0.to(torch.float64).contiguous().clone()
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    imgs = [_image(I, 3, "I"), _image(alpha, 1, "alpha")]
+    _check(load().fg_minimiser_cg(ctypes.byref(imgs[0]), ctypes.byref(imgs[1]),
+                                  ctypes.byref(p) if p is not None else None,
+                                  ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                  int(max_iters), float(rel_tol), ctypes.byref(it),
+                                  ctypes.byref(rr), _stream(stream)))
+    return F, B, it.value, rr.value
 
 
 def quality(F_est, F_gt, alpha_gt, stream=None) -> dict:

@@ -364,3 +364,31 @@ def test_composite_closed_forms():
     assert np.array_equal(out[0, 0], F[0, 0]) and np.array_equal(out[0, 1], Bn[0, 1])
     assert np.allclose(out[0, 2], [0.25 * 1.0 + 0.75 * 0.5, 0.75 * 0.5, 0.25 * 0.25 + 0.75 * 0.75],
                        atol=1e-16)
+
+
+@pytest.mark.parametrize("shape", [(5, 7), (1, 9), (8, 3)])
+def test_sparse_minimiser_equals_dense_assembly(shape):
+    # the oracle's vectorised sparse system against the edge-by-edge dense assembly above
+    pytest.importorskip("scipy.sparse")
+    from oracle import minimiser
+    h, w = shape
+    rng = np.random.default_rng(31 + h * w)
+    a = rng.random((h, w))
+    I = rng.random((h, w, 3))
+    for eps, om in ((5e-3, 0.1), (0.02, 1.0)):
+        Fd, Bd = _dense_minimiser(I, a, eps, om)
+        Fs, Bs = minimiser.minimiser(I, a, eps, om)
+        assert np.abs(Fs - Fd).max() < 1e-10 and np.abs(Bs - Bd).max() < 1e-10
+        assert minimiser.gradient_norm(I, a, Fs, Bs, eps, om) < 1e-10
+
+
+def test_minimiser_is_the_limit_of_the_unclamped_iteration():
+    pytest.importorskip("scipy.sparse")
+    from oracle import minimiser
+    rng = np.random.default_rng(4)
+    a = rng.random((9, 11))
+    I = rng.random((9, 11, 3))
+    Fm, Bm = minimiser.minimiser(I, a)
+    F, B = oracle.level_iterate(I, a, np.zeros((9, 11, 3)), np.zeros((9, 11, 3)), 3000,
+                                Params(clamp=False, order=REDBLACK))
+    assert np.abs(F - Fm).max() < 1e-9 and np.abs(B - Bm).max() < 1e-9
