@@ -297,56 +297,78 @@ EncodeTiledFn encode_tiled() {
 // A 2D tensor map of `rows` rows of `inner8` 8-byte elements, `pitch` bytes apart, with
 // a one-row box of `box8` elements (for gather-mode copies); false if the layout does
 // not allow tensor copies (base or pitch off the 16-byte grid, box too wide).
-bool make_map(CUtensorMap *m, const void *base, long long inner8, long long rows, long long pitch,
-              int box8) {
+// A tensor map over `rows` rows of `inner` elements of `unit` bytes (8, 4 or 2: the
+// element type only sets the addressing granularity), boxes of `box` x 1 elements.
+bool make_map(CUtensorMap *m, const void *base, long long inner, long long rows, long long pitch,
+              int box, int unit) {
     EncodeTiledFn fn = encode_tiled();
-    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (pitch & 15) || box8 > 256 || box8 < 2 ||
-        (box8 & 1) || inner8 < 1 || inner8 * 8 > pitch)
+    const CUtensorMapDataType ty = unit == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64
+                                 : unit == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32
+                                             : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    if (!fn || (unit != 8 && unit != 4 && unit != 2) || (reinterpret_cast<uintptr_t>(base) & 15) ||
+        (pitch & 15) || box > 256 || box < 1 || (box * unit) % 16 || inner < 1 || inner * unit > pitch)
         return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)inner8, (cuuint64_t)rows};
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-    const cuuint32_t box[2] = {(cuuint32_t)box8, 1};
+    const cuuint32_t boxd[2] = {(cuuint32_t)box, 1};
     const cuuint32_t estr[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(base), dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    return fn(m, ty, 2, const_cast<void *>(base), dims, strides, boxd, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Element unit, box width and row length (in units) for a tensor whose rows hold
+// `rowbytes` bytes and whose strips span `span` bytes: the largest unit (8, 4, 2) that
+// divides the row (or, for a padded state, whose rounded-up row stays inside the pitch)
+// and gives a box of at most 256 elements.
+bool pick_unit(long long rowbytes, int span, bool padded, long long pitch, int &unit, int &box,
+               long long &inner) {
+    for (int u : {8, 4, 2}) {
+        const int g = 16 / u;
+        const int b = ((15 + span + u - 1) / u + g - 1) / g * g;
+        if (b > 256) continue;
+        if (rowbytes % u == 0) {
+            inner = rowbytes / u;
+        } else if (padded && (rowbytes + u - 1) / u * u <= pitch) {
+            inner = (rowbytes + u - 1) / u;
+        } else {
+            continue;
+        }
+        unit = u;
+        box = b;
+        return true;
+    }
+    return false;
 }
 
 // Fills the tile-variant fields of `a` and builds its maps; false if not applicable.
 bool plan_tile(int dtype, const Input &in, const State &src, PassArgs &a, TileMaps &m) {
     const int es = dtype == kF32 ? 4 : 2;
-    auto up = [](int v, int k) { return (v + k - 1) / k * k; };
     auto r128 = [](int v) { return (v + 127) & ~127; };
     const int spanI = strip_span(in.w, a.w), spanS = strip_span(src.w, a.w);
-    a.tile_bwI = up((15 + 3 * spanI * es + 7) / 8, 2);
-    a.tile_bwA = up((15 + spanI * es + 7) / 8, 2);
-    a.tile_bwS = up((15 + 3 * spanS * es + 7) / 8, 2);
-    if (a.tile_bwI > 256 || a.tile_bwA > 256 || a.tile_bwS > 256) return false;
-    // rows as whole 8-byte elements: exact for I and alpha; for a padded workspace
-    // state the last partial element lies inside the row's padding
     const long long rbI = 3LL * in.w * es, rbA = (long long)in.w * es, rbS = 3LL * src.w * es;
-    if (rbI % 8 || rbA % 8) return false;
-    long long inS = rbS / 8;
-    if (rbS % 8) {
-        if (!src.padded || (rbS + 7) / 8 * 8 > src.pitch * es) return false;
-        inS = (rbS + 7) / 8;
-    }
+    long long inI, inA, inS;
+    if (!pick_unit(rbI, 3 * spanI * es, false, in.I_pitch * es, a.tile_uI, a.tile_bwI, inI) ||
+        !pick_unit(rbA, spanI * es, false, in.A_pitch * es, a.tile_uA, a.tile_bwA, inA) ||
+        !pick_unit(rbS, 3 * spanS * es, src.padded, src.pitch * es, a.tile_uS, a.tile_bwS, inS))
+        return false;
     const int R = level_pass_tile_rows();
-    a.tile_offA = r128(R * a.tile_bwI * 8);
-    a.tile_offF = a.tile_offA + r128(R * a.tile_bwA * 8);
-    a.tile_offB = a.tile_offF + r128(R * a.tile_bwS * 8);
-    a.tile_chunk = a.tile_offB + r128(R * a.tile_bwS * 8);
-    a.tile_tx = R * 8 * (a.tile_bwI + a.tile_bwA + 2 * a.tile_bwS);
+    const int rowI = a.tile_bwI * a.tile_uI, rowA = a.tile_bwA * a.tile_uA, rowS = a.tile_bwS * a.tile_uS;
+    a.tile_offA = r128(R * rowI);
+    a.tile_offF = a.tile_offA + r128(R * rowA);
+    a.tile_offB = a.tile_offF + r128(R * rowS);
+    a.tile_chunk = a.tile_offB + r128(R * rowS);
+    a.tile_tx = R * (rowI + rowA + 2 * rowS);
     if (level_pass_tile_smem(a.tile_chunk, 3) <= kRingSmemBudget)
         a.tile_slots = 3;
     else if (level_pass_tile_smem(a.tile_chunk, 2) <= kRingSmemBudget)
         a.tile_slots = 2;
     else
         return false;
-    return make_map(&m.I, in.I, rbI / 8, in.h, in.I_pitch * es, a.tile_bwI) &&
-           make_map(&m.A, in.A, rbA / 8, in.h, in.A_pitch * es, a.tile_bwA) &&
-           make_map(&m.F, src.F, inS, src.h, src.pitch * es, a.tile_bwS) &&
-           make_map(&m.B, src.B, inS, src.h, src.pitch * es, a.tile_bwS);
+    return make_map(&m.I, in.I, inI, in.h, in.I_pitch * es, a.tile_bwI, a.tile_uI) &&
+           make_map(&m.A, in.A, inA, in.h, in.A_pitch * es, a.tile_bwA, a.tile_uA) &&
+           make_map(&m.F, src.F, inS, src.h, src.pitch * es, a.tile_bwS, a.tile_uS) &&
+           make_map(&m.B, src.B, inS, src.h, src.pitch * es, a.tile_bwS, a.tile_uS);
 }
 
 // Compositing epilogue of the last pass of a solve (fg_estimate_composite).

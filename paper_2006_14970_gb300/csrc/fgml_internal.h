@@ -58,8 +58,10 @@ struct PassArgs {
     int capI, capA, capS, slot_bytes;
     // row-ring variant only: one past the last byte of I, alpha, Fs and Bs
     const void *I_end, *A_end, *Fs_end, *Bs_end;
-    // tile variant only: box widths (8-byte elements), chunk layout (bytes), chunks in flight
+    // tile variant only: box widths (in elements of tile_u* bytes: 8, 4 or 2, the largest
+    // unit that divides a row), chunk layout (bytes), chunks in flight
     int tile_bwI, tile_bwA, tile_bwS, tile_slots;
+    int tile_uI, tile_uA, tile_uS;
     int tile_offA, tile_offF, tile_offB, tile_chunk, tile_tx;
     // optional compositing epilogue (In == nullptr: none): as the pass stores F it also
     // writes In = alpha F + (1 - alpha) Bn at the same pixel, alpha being the level's

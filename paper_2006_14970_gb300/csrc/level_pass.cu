@@ -789,10 +789,10 @@ struct TileSource {
         }
         const int es = (int)sizeof(T);
         const uint32_t base = slots_s + (uint32_t)gslot * (uint32_t)p.tile_chunk;
-        const uint32_t I = base + (uint32_t)(j * p.tile_bwI * 8);
-        const uint32_t A = base + (uint32_t)p.tile_offA + (uint32_t)(j * p.tile_bwA * 8);
-        const uint32_t F = base + (uint32_t)p.tile_offF + (uint32_t)(j * p.tile_bwS * 8);
-        const uint32_t B = base + (uint32_t)p.tile_offB + (uint32_t)(j * p.tile_bwS * 8);
+        const uint32_t I = base + (uint32_t)(j * p.tile_bwI * p.tile_uI);
+        const uint32_t A = base + (uint32_t)p.tile_offA + (uint32_t)(j * p.tile_bwA * p.tile_uA);
+        const uint32_t F = base + (uint32_t)p.tile_offF + (uint32_t)(j * p.tile_bwS * p.tile_uS);
+        const uint32_t B = base + (uint32_t)p.tile_offB + (uint32_t)(j * p.tile_bwS * p.tile_uS);
         o.a0 = lds<T>(A + oA0);
         o.a1 = lds<T>(A + oA1);
 #pragma unroll
@@ -849,21 +849,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, FGML_TILE_MIN_BLOCKS) lev
     src.slots_s = smem_addr(smem) + (uint32_t)(wib * SLOTS * p.tile_chunk);
     src.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * SLOTS * p.tile_chunk) +
                8u * (uint32_t)(wib * SLOTS);
-    // the strip's source column ranges; box x is the first source byte rounded down to 16
+    // the strip's source column ranges; box x is the first source byte rounded down to 16,
+    // in elements of the tensor map's unit
     const int es = (int)sizeof(T);
     const int X0 = g.x - 2 * lane;
     const int xf = min(max(X0, 0), p.w - 1);
     const int giF = nearest_src(xf, p.Iw, p.w);
     const int gsF = nearest_src(xf, p.sw, p.w);
-    src.xI = (3 * giF * es) / 16 * 2;
-    src.xA = (giF * es) / 16 * 2;
-    src.xS = (3 * gsF * es) / 16 * 2;
-    src.oI0 = 3 * g.gi0 * es - 8 * src.xI;
-    src.oI1 = 3 * g.gi1 * es - 8 * src.xI;
-    src.oA0 = g.gi0 * es - 8 * src.xA;
-    src.oA1 = g.gi1 * es - 8 * src.xA;
-    src.oS0 = 3 * g.gs0 * es - 8 * src.xS;
-    src.oS1 = 3 * g.gs1 * es - 8 * src.xS;
+    src.xI = (3 * giF * es) / 16 * (16 / p.tile_uI);
+    src.xA = (giF * es) / 16 * (16 / p.tile_uA);
+    src.xS = (3 * gsF * es) / 16 * (16 / p.tile_uS);
+    src.oI0 = 3 * g.gi0 * es - p.tile_uI * src.xI;
+    src.oI1 = 3 * g.gi1 * es - p.tile_uI * src.xI;
+    src.oA0 = g.gi0 * es - p.tile_uA * src.xA;
+    src.oA1 = g.gi1 * es - p.tile_uA * src.xA;
+    src.oS0 = 3 * g.gs0 * es - p.tile_uS * src.xS;
+    src.oS1 = 3 * g.gs1 * es - p.tile_uS * src.xS;
     if (lane == 0) {
         for (int s = 0; s < SLOTS; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(src.bar0 + 8u * s) : "memory");

@@ -2,10 +2,12 @@
 
     python -m paper_2006_14970_gb300.profile_case level_pass 4096 2304 [--repeat 4]
     python -m paper_2006_14970_gb300.profile_case estimate 2048 1536 [--dtype bf16]
+    python -m paper_2006_14970_gb300.profile_case batch 64 0
 
 level_pass: the top-level pass of a W x H image (sweeps of the top level, starting F/B
 gathered from the level below it), the dominant launch of a solve.
 estimate: complete fg_estimate calls.
+batch: fg_estimate_batch of the first W images of the 64-image batched workload (H unused).
 Inputs come from the seeded synthetic generator; nothing is checked here.
 """
 from __future__ import annotations
@@ -19,7 +21,7 @@ from . import build as _build
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["level_pass", "estimate"])
+    ap.add_argument("case", choices=["level_pass", "estimate", "batch"])
     ap.add_argument("w", type=int)
     ap.add_argument("h", type=int)
     ap.add_argument("--repeat", type=int, default=4)
@@ -36,12 +38,21 @@ def main():
         kw["big_iters"] = a.big_iters
     prm = fgml.params(**kw) if kw else None
     dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
-    s = synth.make_sample(a.w, a.h, synth.SEED_BASE + 50)
-    I = torch.from_numpy(s.I).cuda().to(dt)
-    A = torch.from_numpy(s.alpha).cuda().to(dt)
+    if a.case != "batch":
+        s = synth.make_sample(a.w, a.h, synth.SEED_BASE + 50)
+        I = torch.from_numpy(s.I).cuda().to(dt)
+        A = torch.from_numpy(s.alpha).cuda().to(dt)
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
-    if a.case == "level_pass":
+    if a.case == "batch":
+        ss = synth.batch(64)[:a.w]
+        imgs = [(torch.from_numpy(t.I).cuda().to(dt), torch.from_numpy(t.alpha).cuda().to(dt))
+                for t in ss]
+        outs = [(torch.empty_like(I), torch.empty_like(I)) for I, _ in imgs]
+
+        def run():
+            fgml.estimate_batch(imgs, prm, outs)
+    elif a.case == "level_pass":
         levels = fgml.schedule(a.w, a.h)
         (pw, ph, _), (_, _, k) = levels[-2], levels[-1]
         g = torch.Generator(device="cuda").manual_seed(1)
