@@ -151,6 +151,7 @@ struct Workspace {
     Buf batch;    // work lists and per-image levels of fg_estimate_batch
     Buf aux;      // per-block partial sums of fg_quality
     Buf cg;       // vectors of fg_minimiser_cg
+    Buf align;    // copies of I and alpha with rows on the 16-byte grid (tensor maps need it)
     // launch sequences of fg_estimate captured as CUDA graphs, by call signature
     std::map<std::string, cudaGraphExec_t> graphs;
     std::vector<std::string> graph_order;   // oldest first, for eviction
@@ -246,6 +247,7 @@ struct Input {
     const void *I, *A;
     long long I_pitch, A_pitch;   // elements
     int w, h;
+    bool padded = false;          // rows readable up to the pitch (the library's aligned copies)
 };
 
 // Rows per warp of a level pass: one wave of resident warps (two 4-warp blocks per SM)
@@ -348,8 +350,8 @@ bool plan_tile(int dtype, const Input &in, const State &src, PassArgs &a, TileMa
     const int spanI = strip_span(in.w, a.w), spanS = strip_span(src.w, a.w);
     const long long rbI = 3LL * in.w * es, rbA = (long long)in.w * es, rbS = 3LL * src.w * es;
     long long inI, inA, inS;
-    if (!pick_unit(rbI, 3 * spanI * es, false, in.I_pitch * es, a.tile_uI, a.tile_bwI, inI) ||
-        !pick_unit(rbA, spanI * es, false, in.A_pitch * es, a.tile_uA, a.tile_bwA, inA) ||
+    if (!pick_unit(rbI, 3 * spanI * es, in.padded, in.I_pitch * es, a.tile_uI, a.tile_bwI, inI) ||
+        !pick_unit(rbA, spanI * es, in.padded, in.A_pitch * es, a.tile_uA, a.tile_bwA, inA) ||
         !pick_unit(rbS, 3 * spanS * es, src.padded, src.pitch * es, a.tile_uS, a.tile_bwS, inS))
         return false;
     const int R = level_pass_tile_rows();
@@ -473,11 +475,28 @@ fg_status run_level(int dtype, const fg_params &p, const Input &in, State &src, 
     return FG_OK;
 }
 
+// Rows a tensor map can describe: base and pitch (bytes) on the 16-byte grid.
+bool rows_on_grid(const void *ptr, long long pitch_bytes) {
+    return ((uintptr_t)ptr & 15) == 0 && (pitch_bytes & 15) == 0;
+}
+
 // The kernels of one solve, enqueued on `s` (no allocation, no synchronisation).
 fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
                           const std::vector<Level> &lv, int nc, void *Fd, void *Bd,
                           long long d_pitch, Workspace &ws, int es, cudaStream_t s,
-                          const Composite *cmp = nullptr) {
+                          const Composite *cmp = nullptr, const Input *staged_from = nullptr) {
+    if (staged_from) {
+        // I and alpha into their row-aligned copies (`in` describes the copies)
+        const Input &o = *staged_from;
+        StageList L;
+        std::memset(&L, 0, sizeof L);
+        L.local[0] = StageJob{o.I, const_cast<void *>(in.I), o.I_pitch * es, in.I_pitch * es,
+                              3LL * o.w * es, o.h, 0};
+        L.local[1] = StageJob{o.A, const_cast<void *>(in.A), o.A_pitch * es, in.A_pitch * es,
+                              (long long)o.w * es, o.h, o.h};
+        cudaError_t e = launch_stage_rows(dtype, L, 2, 2LL * o.h, s);
+        if (e != cudaSuccess) return cuda_fail(e, "row-aligned copy of the inputs");
+    }
     const int n = (int)lv.size();
     CoarseArgs ca;
     std::memset(&ca, 0, sizeof ca);
@@ -567,7 +586,15 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
             need = std::max(need, state_bytes(lv[l].w, lv[l].h, es));
     }
     Workspace &ws = workspace_for(s);
-    if (need && (ws.lev[0].bytes < need || ws.lev[1].bytes < need)) {
+    // Rows off the 16-byte grid cannot be described by tensor maps: the level passes of a
+    // large image then read a row-aligned copy of I and alpha (one copy kernel, 32 bytes
+    // per pixel in FP32) instead of falling back to per-row copies.
+    const bool stage = n > nc && (long long)in.w * in.h > small_level_pixels() &&
+                       !(rows_on_grid(in.I, in.I_pitch * es) && rows_on_grid(in.A, in.A_pitch * es));
+    const long long pI = ((3LL * in.w * es + 15) & ~15LL) / es, pA = (((long long)in.w * es + 15) & ~15LL) / es;
+    const size_t offA = align256((size_t)(pI * es) * in.h);
+    const size_t stage_need = stage ? offA + align256((size_t)(pA * es) * in.h) : 0;
+    if ((need && (ws.lev[0].bytes < need || ws.lev[1].bytes < need)) || ws.align.bytes < stage_need) {
         // cached graphs point at the buffers about to be replaced
         cudaStreamSynchronize(s);
         clear_graphs(ws);
@@ -575,9 +602,20 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
         if (st != FG_OK) return st;
         st = ensure(ws.lev[1], need, s);
         if (st != FG_OK) return st;
+        st = ensure(ws.align, stage_need, s);
+        if (st != FG_OK) return st;
     }
+    Input run = in;
+    if (stage) {
+        run.I = ws.align.p;
+        run.A = static_cast<char *>(ws.align.p) + offA;
+        run.I_pitch = pI;
+        run.A_pitch = pA;
+        run.padded = true;
+    }
+    const Input *from = stage ? &in : nullptr;
     if (!graphs_enabled())
-        return launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp);
+        return launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp, from);
 
     // the launch sequence depends on the pointers, pitches, sizes, dtype and parameters
     struct {
@@ -614,9 +652,9 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
         cudaStream_t cs = capture_stream();
         if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
-            return launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp);
+            return launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp, from);
         }
-        fg_status st = launch_sequence(in, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, cs, cmp);
+        fg_status st = launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, cs, cmp, from);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         if (st != FG_OK) {
@@ -975,6 +1013,7 @@ fg_status fg_release_workspace(void *stream) {
     cudaFree(w.batch.p);
     cudaFree(w.aux.p);
     cudaFree(w.cg.p);
+    cudaFree(w.align.p);
     return FG_OK;
 }
 
@@ -1126,6 +1165,8 @@ extern "C" fg_status fg_estimate_noalloc(const fg_image *I, const fg_image *alph
 namespace {
 
 constexpr int kBatchRingSlotCap = 4096;        // largest ring slot a batch pass may use
+constexpr int kBatchRegionCap = 27 * 1024;     // per-warp shared memory of the batch kernel (128 multiple)
+static_assert(kRingSlots * kBatchRingSlotCap <= kBatchRegionCap, "ring slots exceed the region");
 constexpr long long kBatchWaitNs = 2000000000; // bound of one dependency wait (2 s)
 
 // Rows per strip of a batch pass: a few waves of the persistent grid per level.
@@ -1233,10 +1274,14 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
         int nc;
         size_t need;
         size_t buf_off;
+        bool stage;            // rows off the 16-byte grid: levels read a row-aligned copy
+        size_t stage_off, stage_offA;
+        long long pI, pA;      // pitches of the copy (elements)
     };
     std::vector<Img> im(n);
     bool zero_sweeps = false;
     size_t buf_total = 0;
+    int nstage = 0;
     for (int i = 0; i < n; ++i) {
         Img &m = im[i];
         m.in = Input{I[i].ptr, alpha[i].ptr, I[i].row_pitch_bytes / es, alpha[i].row_pitch_bytes / es,
@@ -1254,6 +1299,17 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
         m.need = align256(m.need);
         m.buf_off = buf_total;
         buf_total += 2 * m.need;
+        m.stage = m.nc < nl && !(rows_on_grid(m.in.I, m.in.I_pitch * es) &&
+                                 rows_on_grid(m.in.A, m.in.A_pitch * es));
+        if (m.stage) {
+            m.pI = ((3LL * m.in.w * es + 15) & ~15LL) / es;
+            m.pA = (((long long)m.in.w * es + 15) & ~15LL) / es;
+            m.stage_off = buf_total;
+            m.stage_offA = align256((size_t)(m.pI * es) * m.in.h);
+            buf_total += m.stage_offA + align256((size_t)(m.pA * es) * m.in.h);
+            ++nstage;
+
+        }
     }
     if (zero_sweeps || p.order != FG_ORDER_JACOBI) {
         // levels without sweeps are plain resizes, and the work-list kernel runs the Jacobi
@@ -1285,7 +1341,8 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
                           ((h + sh - 1) / sh);
             }
     if (nitems > (1LL << 30)) return fail(FG_ERR_INVALID_ARG, "batch too large");
-    const size_t off_coarse = 0;
+    const size_t off_jobs = 0;
+    const size_t off_coarse = align256(off_jobs + 2 * nstage * sizeof(StageJob));
     const size_t off_desc = align256(off_coarse + n * sizeof(CoarseArgs));
     const size_t off_items = align256(off_desc + ndesc * sizeof(BatchDesc));
     const size_t off_cnt = align256(off_items + nitems * sizeof(BatchItem));
@@ -1294,10 +1351,28 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
     if ((st = ensure(ws.batch, off_bufs + buf_total + 256, s)) != FG_OK) return st;
     char *dev = (char *)ws.batch.p;
 
-    int slot_max = 16;
+    int slot_max = 16, tile_max = 0;
+    std::vector<StageJob> jobs;
+    long long stage_rows = 0;
     for (int i = 0; i < n; ++i) {
         Img &m = im[i];
         const int nl = (int)m.lv.size();
+        if (m.stage) {
+            char *sb = dev + off_bufs + m.stage_off;
+            Input c = m.in;
+            c.I = sb;
+            c.A = sb + m.stage_offA;
+            c.I_pitch = m.pI;
+            c.A_pitch = m.pA;
+            c.padded = true;
+            jobs.push_back(StageJob{m.in.I, sb, m.in.I_pitch * es, m.pI * es, 3LL * m.in.w * es, m.in.h,
+                                    stage_rows});
+            stage_rows += m.in.h;
+            jobs.push_back(StageJob{m.in.A, sb + m.stage_offA, m.in.A_pitch * es, m.pA * es,
+                                    (long long)m.in.w * es, m.in.h, stage_rows});
+            stage_rows += m.in.h;
+            m.in = c;
+        }
         Buf b0{dev + off_bufs + m.buf_off, m.need}, b1{dev + off_bufs + m.buf_off + m.need, m.need};
         const Buf *bufs[2] = {&b0, &b1};
         CoarseArgs &ca = coarse[i];
@@ -1361,6 +1436,14 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
                 d.iters = passes[j];
                 d.dep = prev;
                 d.dep_count = prev >= 0 ? descs[prev].a.n_warps : 0;
+                // rows by TMA gather where the pass's tensor maps exist and its chunks fit
+                // the per-warp region; else the ring, else plain loads
+                if (d.iters > 0 && plan_tile(dtype, m.in, src, d.a, d.maps) &&
+                    (long long)kBatchTileSlots * d.a.tile_chunk <= kBatchRegionCap) {
+                    d.tile = 1;
+                    tile_max = std::max(tile_max, kBatchTileSlots * d.a.tile_chunk);
+                    ring = false;
+                }
                 d.ring = ring ? 1 : 0;
                 if (ring) slot_max = std::max(slot_max, d.a.slot_bytes);
                 prev = (int)descs.size();
@@ -1392,11 +1475,19 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
         }
 
     std::vector<char> blob(off_bufs, 0);
+    if (!jobs.empty()) std::memcpy(blob.data() + off_jobs, jobs.data(), jobs.size() * sizeof(StageJob));
     std::memcpy(blob.data() + off_coarse, coarse.data(), n * sizeof(CoarseArgs));
     if (!descs.empty()) std::memcpy(blob.data() + off_desc, descs.data(), descs.size() * sizeof(BatchDesc));
     if (!items.empty()) std::memcpy(blob.data() + off_items, items.data(), items.size() * sizeof(BatchItem));
     cudaError_t e = cudaMemcpyAsync(dev, blob.data(), blob.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy of the batch work list");
+    if (!jobs.empty()) {
+        StageList L;
+        std::memset(&L, 0, sizeof L);
+        L.dev = reinterpret_cast<const StageJob *>(dev + off_jobs);
+        e = launch_stage_rows(dtype, L, (int)jobs.size(), stage_rows, s);
+        if (e != cudaSuccess) return cuda_fail(e, "row-aligned copies of the batch inputs");
+    }
     e = launch_coarse_batch(dtype, p.clamp, reinterpret_cast<const CoarseArgs *>(dev + off_coarse), n,
                             max_total, s);
     if (e != cudaSuccess) return cuda_fail(e, "batched coarse kernel launch");
@@ -1408,6 +1499,9 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
     b.counters = reinterpret_cast<int *>(dev + off_cnt);
     b.wait_ns = kBatchWaitNs;
     b.slot_bytes = slot_max;
+    // 128-byte aligned, as the tensor copies into a warp's region require
+    b.region = (std::max(kRingSlots * slot_max, tile_max) + 127) & ~127;
+    if (b.region > kBatchRegionCap) return fail(FG_ERR_CUDA, "batch region %d exceeds the cap", b.region);
     return batch_launch(dtype, p.clamp, b, s);
 }
 
@@ -1415,7 +1509,8 @@ extern "C" fg_status fg_selftest_bounded_wait(void *stream) {
     g_err.clear();
     cudaStream_t s = (cudaStream_t)stream;
     Workspace &ws = workspace_for(s);
-    fg_status st = ensure(ws.batch, 4096, s);
+    const size_t off_item = align256(sizeof(BatchDesc)), off_cnt = off_item + 256;
+    fg_status st = ensure(ws.batch, off_cnt + 256, s);
     if (st != FG_OK) return st;
     // one item that waits for its own pass: the count it waits for is never reached
     BatchDesc d;
@@ -1425,18 +1520,19 @@ extern "C" fg_status fg_selftest_bounded_wait(void *stream) {
     d.dep_count = 1;
     BatchItem it{0, 0};
     char *dev = (char *)ws.batch.p;
-    std::vector<char> blob(1024, 0);
+    std::vector<char> blob(off_cnt + 256, 0);
     std::memcpy(blob.data(), &d, sizeof d);
-    std::memcpy(blob.data() + 512, &it, sizeof it);
+    std::memcpy(blob.data() + off_item, &it, sizeof it);
     cudaError_t e = cudaMemcpyAsync(dev, blob.data(), blob.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "self-test upload");
     BatchLaunch b;
     b.descs = reinterpret_cast<const BatchDesc *>(dev);
-    b.items = reinterpret_cast<const BatchItem *>(dev + 512);
+    b.items = reinterpret_cast<const BatchItem *>(dev + off_item);
     b.n_items = 1;
-    b.counters = reinterpret_cast<int *>(dev + 768);
+    b.counters = reinterpret_cast<int *>(dev + off_cnt);
     b.wait_ns = 20000000;   // 20 ms
     b.slot_bytes = 16;
+    b.region = (kRingSlots * 16 + 127) & ~127;
     b.blocks = 1;
     e = launch_level_batch(kF32, 1, b, s, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "self-test launch");

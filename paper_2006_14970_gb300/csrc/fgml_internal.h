@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cstdint>
+#include <algorithm>
 #include <utility>
 
 namespace fgml {
@@ -82,12 +83,18 @@ __device__ __forceinline__ void composite_px(const void *Bn, long long bn_pitch,
 }
 
 // One level pass of a work-list batch.
+struct TileMaps {
+    CUtensorMap I, A, F, B;
+};
+
 struct BatchDesc {
     PassArgs a;
     int iters;       // sweeps of this pass (1 or 2)
     int dep;         // pass whose strips must all be done first (-1: none)
     int dep_count;   // strips of that pass
-    int ring;        // 1: rows through the TMA ring (a.cap*/slot_bytes set), 0: plain loads
+    int ring;        // 1: rows through the TMA ring (a.cap*/slot_bytes set)
+    int tile;        // 1: rows by TMA gather from `maps` (a.tile_* set); else ring or plain loads
+    TileMaps maps;   // the pass's tensor maps (64-byte aligned in the device array)
 };
 
 // One work item: strip `warp` of pass `desc`.
@@ -102,8 +109,30 @@ struct BatchLaunch {
     int *counters;       // [0]: next item to pop, [1 + d]: finished strips of pass d
     long long wait_ns;   // bound of one dependency wait
     int slot_bytes;      // ring slot size (largest over the ring passes, >= 16)
+    int region;          // shared-memory bytes per warp (ring slots or tile chunks)
     int blocks;          // persistent grid (at most the resident blocks)
 };
+
+// One row-aligned copy (stage.cu): `rows` rows of `row_bytes` from src (pitch src_pitch
+// bytes) to dst (pitch dst_pitch, a multiple of 16; dst 16-byte aligned).
+struct StageJob {
+    const void *src;
+    void *dst;
+    long long src_pitch, dst_pitch, row_bytes, rows;
+    long long row0;   // first row of this job among the rows of all jobs of the launch
+};
+// The jobs of one launch: a device array, or (dev == nullptr) up to two by value.
+struct StageList {
+    const StageJob *dev;
+    StageJob local[2];
+};
+// Runs the jobs in one launch; total_rows = the rows of all jobs.
+cudaError_t launch_stage_rows(int dtype, const StageList &list, int njobs, long long total_rows,
+                              cudaStream_t s);
+
+// Tile chunks in flight per warp in the work-list kernel.
+constexpr int kBatchTileSlots = 3;
+size_t level_batch_smem(int region);
 
 // Launches the batch kernel, or (blocks_per_sm != NULL) only reports its occupancy.
 cudaError_t launch_level_batch(int dtype, int clamp, const BatchLaunch &b, cudaStream_t s,
@@ -111,10 +140,6 @@ cudaError_t launch_level_batch(int dtype, int clamp, const BatchLaunch &b, cudaS
 
 // Tensor maps of the tile variant: I, alpha, and the starting F and B, as 2D tensors of
 // 8-byte elements (a row's bytes / 8), box one row high for gather-mode copies.
-struct TileMaps {
-    CUtensorMap I, A, F, B;
-};
-
 // Largest source-column span (in pixels) of one warp strip of a level pass, for a gather
 // from a side of length S to a level side of length D (host planning of ring slots).
 int strip_span(int S, int D);

@@ -701,7 +701,8 @@ struct TileSource {
     int xI, xA, xS;         // box x coordinates (8-byte elements; even)
     int oI0, oI1, oA0, oA1, oS0, oS1;   // per-lane byte offsets of the two pixels in box rows
     int r_first;
-    int cfill;              // next chunk to fill
+    int cfill;              // chunks filled so far (counted across the strips of a warp)
+    int cbase;              // cfill when the current strip started
     int j;                  // row of the current chunk being taken
     int gslot;              // slot of the current chunk
     uint32_t gpar;
@@ -715,7 +716,7 @@ struct TileSource {
         int gy[kTileRows], sy[kTileRows];
 #pragma unroll
         for (int k = 0; k < kTileRows; ++k) {
-            const int r = r_first + cfill * kTileRows + k;
+            const int r = r_first + (cfill - cbase) * kTileRows + k;
             if (r <= ct.r_last) {
                 gy[k] = fI.next();
                 sy[k] = fS.next();
@@ -763,12 +764,44 @@ struct TileSource {
         return __all_sync(kFull, ok != 0);
     }
 
-    __device__ __forceinline__ void start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
-        r_first = ct.r_first;
+    // Slot and phase counters (cfill, gslot, gpar) start at 0 once per warp (init) and run
+    // on across strips, so the mbarriers are initialised once; every strip takes all the
+    // chunks it fills, so nothing is in flight between strips.
+    // A strip's maps, box x coordinates (the first source byte rounded down to 16, in
+    // elements of the map's unit) and the lane's byte offsets inside the box rows.
+    __device__ __forceinline__ void setup(const PassArgs &p, const LaneGeo &g, const CUtensorMap *I_,
+                                          const CUtensorMap *A_, const CUtensorMap *F_,
+                                          const CUtensorMap *B_) {
+        mI = I_;
+        mA = A_;
+        mF = F_;
+        mB = B_;
+        const int es = (int)sizeof(T);
+        const int X0 = g.x - 2 * lane;
+        const int xf = min(max(X0, 0), p.w - 1);
+        const int giF = nearest_src(xf, p.Iw, p.w);
+        const int gsF = nearest_src(xf, p.sw, p.w);
+        xI = (3 * giF * es) / 16 * (16 / p.tile_uI);
+        xA = (giF * es) / 16 * (16 / p.tile_uA);
+        xS = (3 * gsF * es) / 16 * (16 / p.tile_uS);
+        oI0 = 3 * g.gi0 * es - p.tile_uI * xI;
+        oI1 = 3 * g.gi1 * es - p.tile_uI * xI;
+        oA0 = g.gi0 * es - p.tile_uA * xA;
+        oA1 = g.gi1 * es - p.tile_uA * xA;
+        oS0 = 3 * g.gs0 * es - p.tile_uS * xS;
+        oS1 = 3 * g.gs1 * es - p.tile_uS * xS;
+    }
+
+    __device__ __forceinline__ void init() {
         cfill = 0;
-        j = 0;
         gslot = 0;
         gpar = 0;
+    }
+
+    __device__ __forceinline__ void start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
+        r_first = ct.r_first;
+        cbase = cfill;
+        j = 0;
         issued = parity = 0;
         fI.init(ct.r_first, p.Ih, p.h);
         fS.init(ct.r_first, p.sh, p.h);
@@ -808,7 +841,7 @@ struct TileSource {
             // the chunk is used up: refill its slot with the chunk SLOTS ahead
             __syncwarp();
             j = 0;
-            if (r_first + cfill * kTileRows <= ct.r_last) fill(p, ct);
+            if (r_first + (cfill - cbase) * kTileRows <= ct.r_last) fill(p, ct);
             if (++gslot == SLOTS) {
                 gslot = 0;
                 gpar ^= 1u;
@@ -842,29 +875,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, FGML_TILE_MIN_BLOCKS) lev
     src.sm = smem;
     src.sbase = smem_addr(smem);
     src.lane = lane;
-    src.mI = &mI;
-    src.mA = &mA;
-    src.mF = &mF;
-    src.mB = &mB;
     src.slots_s = smem_addr(smem) + (uint32_t)(wib * SLOTS * p.tile_chunk);
     src.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * SLOTS * p.tile_chunk) +
                8u * (uint32_t)(wib * SLOTS);
-    // the strip's source column ranges; box x is the first source byte rounded down to 16,
-    // in elements of the tensor map's unit
-    const int es = (int)sizeof(T);
-    const int X0 = g.x - 2 * lane;
-    const int xf = min(max(X0, 0), p.w - 1);
-    const int giF = nearest_src(xf, p.Iw, p.w);
-    const int gsF = nearest_src(xf, p.sw, p.w);
-    src.xI = (3 * giF * es) / 16 * (16 / p.tile_uI);
-    src.xA = (giF * es) / 16 * (16 / p.tile_uA);
-    src.xS = (3 * gsF * es) / 16 * (16 / p.tile_uS);
-    src.oI0 = 3 * g.gi0 * es - p.tile_uI * src.xI;
-    src.oI1 = 3 * g.gi1 * es - p.tile_uI * src.xI;
-    src.oA0 = g.gi0 * es - p.tile_uA * src.xA;
-    src.oA1 = g.gi1 * es - p.tile_uA * src.xA;
-    src.oS0 = 3 * g.gs0 * es - p.tile_uS * src.xS;
-    src.oS1 = 3 * g.gs1 * es - p.tile_uS * src.xS;
+    src.init();
+    src.setup(p, g, &mI, &mA, &mF, &mB);
     if (lane == 0) {
         for (int s = 0; s < SLOTS; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(src.bar0 + 8u * s) : "memory");
@@ -905,25 +920,38 @@ __device__ __forceinline__ bool wait_count(const int *c, int need, long long bud
 template <typename T, bool CLAMP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_batch_kernel(
     const BatchDesc *descs, const BatchItem *items, int n_items, int *counters,
-    long long wait_ns, int slot_bytes) {
+    long long wait_ns, int slot_bytes, int region) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ PassArgs sp[kWarpsPerBlock];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    // per warp: one `region` of bytes shared by the ring slots and the tile chunks (a
+    // strip takes everything it loads, so the two never hold data at the same time), then
+    // the ring's and the tile's mbarriers
+    const uint32_t base = smem_addr(smem) + (uint32_t)(wib * region);
+    const uint32_t bars = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * region);
 
     RingSource<T> ring;
     ring.sm = smem;
     ring.sbase = smem_addr(smem);
     ring.lane = lane;
-    ring.slots_s = smem_addr(smem) + (uint32_t)(wib * kRingSlots * slot_bytes);
-    ring.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * kRingSlots * slot_bytes) +
-                8u * (uint32_t)(wib * kRingSlots);
+    ring.slots_s = base;
+    ring.bar0 = bars + 8u * (uint32_t)(wib * kRingSlots);
     ring.fslot = ring.gslot = 0;
     ring.fpar = ring.gpar = 0;
     ring.issued = ring.parity = 0;
+    TileSource<T, kBatchTileSlots> tile;
+    tile.sm = smem;
+    tile.sbase = smem_addr(smem);
+    tile.lane = lane;
+    tile.slots_s = base;
+    tile.bar0 = bars + 8u * (uint32_t)(kWarpsPerBlock * kRingSlots + wib * kBatchTileSlots);
+    tile.init();
     if (lane == 0) {
         for (int s = 0; s < kRingSlots; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(ring.bar0 + 8u * s) : "memory");
+        for (int s = 0; s < kBatchTileSlots; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tile.bar0 + 8u * s) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
@@ -938,7 +966,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_batch_kernel(
         const int *src_words = reinterpret_cast<const int *>(&d.a);
         int *dst_words = reinterpret_cast<int *>(&sp[wib]);
         for (int k = lane; k < (int)(sizeof(PassArgs) / sizeof(int)); k += 32) dst_words[k] = src_words[k];
-        const int iters = d.iters, dep = d.dep, dep_count = d.dep_count, use_ring = d.ring;
+        const int iters = d.iters, dep = d.dep, dep_count = d.dep_count, use_ring = d.ring,
+                  use_tile = d.tile;
         __syncwarp();
         const PassArgs &p = sp[wib];
         if (dep >= 0) {
@@ -956,7 +985,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_batch_kernel(
         Ctl ct;
         Out out;
         bool ok;
-        if (use_ring) {
+        if (use_tile) {
+            const TileMaps &m = d.maps;
+            if (iters == 1) {
+                lane_setup<T>(p, it.warp, lane, g, ct, out, 1);
+                tile.setup(p, g, &m.I, &m.A, &m.F, &m.B);
+                ok = run_strip<T, 1, CLAMP>(p, g, ct, out, tile);
+            } else {
+                lane_setup<T>(p, it.warp, lane, g, ct, out, 2);
+                tile.setup(p, g, &m.I, &m.A, &m.F, &m.B);
+                ok = run_strip<T, 2, CLAMP>(p, g, ct, out, tile);
+            }
+        } else if (use_ring) {
             if (iters == 1) {
                 lane_setup<T>(p, it.warp, lane, g, ct, out, 1);
                 ring.setup(p, g, lane);
@@ -1114,7 +1154,7 @@ int level_pass_tile_rows() { return kTileRows; }
 
 template <typename T, bool CLAMP>
 cudaError_t batch_t(const BatchLaunch &b, cudaStream_t s, int *blocks_per_sm) {
-    const size_t smem = level_pass_ring_smem(b.slot_bytes);
+    const size_t smem = level_batch_smem(b.region);
     cudaError_t e = cudaFuncSetAttribute(level_batch_kernel<T, CLAMP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1123,7 +1163,7 @@ cudaError_t batch_t(const BatchLaunch &b, cudaStream_t s, int *blocks_per_sm) {
                                                              kWarpsPerBlock * 32, smem);
     }
     level_batch_kernel<T, CLAMP><<<b.blocks, kWarpsPerBlock * 32, smem, s>>>(
-        b.descs, b.items, b.n_items, b.counters, b.wait_ns, b.slot_bytes);
+        b.descs, b.items, b.n_items, b.counters, b.wait_ns, b.slot_bytes, b.region);
     return cudaGetLastError();
 }
 
@@ -1137,6 +1177,10 @@ cudaError_t launch_level_batch(int dtype, int clamp, const BatchLaunch &b, cudaS
         case kF16: return clamp ? batch_t<__half, true>(b, s, blocks_per_sm) : batch_t<__half, false>(b, s, blocks_per_sm);
     }
     return cudaErrorInvalidValue;
+}
+
+size_t level_batch_smem(int region) {
+    return (size_t)kWarpsPerBlock * (size_t)region + (size_t)kWarpsPerBlock * (kRingSlots + kBatchTileSlots) * 8;
 }
 
 size_t level_pass_ring_smem(int slot_bytes) {

@@ -28,6 +28,7 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--small-iters", type=int, default=None)
     ap.add_argument("--big-iters", type=int, default=None)
+    ap.add_argument("--pad", action="store_true", help="batch: rows of I and alpha padded to 16 bytes")
     a = ap.parse_args()
     _build.build()
     from . import fgml, synth
@@ -46,8 +47,19 @@ def main():
     stop = torch.cuda.Event(enable_timing=True)
     if a.case == "batch":
         ss = synth.batch(64)[:a.w]
-        imgs = [(torch.from_numpy(t.I).cuda().to(dt), torch.from_numpy(t.alpha).cuda().to(dt))
-                for t in ss]
+
+        def dev(x, ch):
+            t = torch.from_numpy(x).cuda().to(dt)
+            if not a.pad:
+                return t
+            h, w = x.shape[0], x.shape[1]
+            q = 16 // t.element_size()
+            pitch = (ch * w + q - 1) // q * q
+            buf = torch.empty((h, pitch), dtype=dt, device="cuda")
+            v = buf[:, :ch * w].view(h, w, ch) if ch > 1 else buf[:, :w]
+            v.copy_(t)
+            return v
+        imgs = [(dev(t.I, 3), dev(t.alpha, 1)) for t in ss]
         outs = [(torch.empty_like(I), torch.empty_like(I)) for I, _ in imgs]
 
         def run():
