@@ -1170,11 +1170,29 @@ static_assert(kRingSlots * kBatchRingSlotCap <= kBatchRegionCap, "ring slots exc
 constexpr long long kBatchWaitNs = 2000000000; // bound of one dependency wait (2 s)
 
 // Rows per strip of a batch pass: a few waves of the persistent grid per level.
+// Rows per strip of a work-list pass: about `per_sm` strips per SM for the level, within
+// [lo, hi] rows (FGML_BATCH_STRIPS="per_sm,lo,hi" overrides the defaults for tuning).
 int batch_strip_rows(int w, int h) {
+    static const int cfg[3] = {4, 8, 64};
+    static int v[3] = {0, 0, 0};
+    static bool init = false;
+    if (!init) {
+        v[0] = cfg[0];
+        v[1] = cfg[1];
+        v[2] = cfg[2];
+        const char *e = std::getenv("FGML_BATCH_STRIPS");
+        int a, b, c;
+        if (e && std::sscanf(e, "%d,%d,%d", &a, &b, &c) == 3 && a > 0 && b > 0 && c >= b) {
+            v[0] = a;
+            v[1] = b;
+            v[2] = c;
+        }
+        init = true;
+    }
     const int nx = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
-    const long long target = (long long)sm_count() * 4;
+    const long long target = (long long)sm_count() * v[0];
     long long r = ((long long)h * nx + target - 1) / target;
-    return (int)std::min<long long>(std::max<long long>(r, 8), 64);
+    return (int)std::min<long long>(std::max<long long>(r, v[1]), v[2]);
 }
 
 
