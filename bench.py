@@ -53,6 +53,23 @@ def _dist():
     return world, rank, local
 
 
+def rank_max(v: float, world: int, device) -> float:
+    """The largest of every rank's v (the slowest rank's time): one all-reduce when the
+    job has several ranks."""
+    if world == 1:
+        return v
+    import torch
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, pixels_per_rank: int, ms: float) -> float:
+    """Whole-job Mpix/s of `world` replicas that each solved `pixels_per_rank` pixels in
+    `ms` milliseconds (the slowest rank's time): weak scaling, no data-path exchange."""
+    return world * pixels_per_rank / (ms * 1e-3) / 1e6
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
 
@@ -351,11 +368,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(v, world, dev)
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -416,7 +429,7 @@ def main():
         roof = top_pass_roofline(w, h, I, A, args.steps, args.warmup,
                                  "level_pass_2048x1536.md")
     clocks = clk.summary()
-    value = world * w * h / (ms * 1e-3) / 1e6
+    value = replica_throughput(world, w * h, ms)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the region
     Ih = torch.from_numpy(s.I).pin_memory()

@@ -186,3 +186,25 @@ def test_unaligned_base_pointers(fgml):
         _assert_close(F.cpu().numpy().astype(np.float64), B.cpu().numpy().astype(np.float64),
                       Fo, Bo, what=f"unaligned {w}x{h}+{off}")
     fgml.sync()   # no bounded wait gave up
+
+
+@pytest.mark.parametrize("wh", [(2047, 1535), (1939, 611)])
+def test_packed_rows_off_the_grid_equal_padded_rows(fgml, wh):
+    # tightly packed rows whose width is not a multiple of 16 bytes go through the
+    # library's row-aligned copy; the same image in 16-byte padded rows does not: both
+    # must give the same bits, and match the oracle
+    w, h = wh
+    s = synth.make_sample(w, h, 4100 + w, hair=True)
+    I = torch.from_numpy(s.I).cuda()
+    A = torch.from_numpy(s.alpha).cuda()
+    pitch = (3 * w + 3) // 4 * 4
+    Ip = torch.zeros((h, pitch), device="cuda")[:, :3 * w].view(h, w, 3)
+    Ap = torch.zeros((h, (w + 3) // 4 * 4), device="cuda")[:, :w]
+    Ip.copy_(I)
+    Ap.copy_(A)
+    F1, B1 = fgml.estimate(I, A)
+    F2, B2 = fgml.estimate(Ip, Ap)
+    torch.cuda.synchronize()
+    assert torch.equal(F1, F2) and torch.equal(B1, B2)
+    Fo, Bo = oracle.ml(s.I, s.alpha)
+    assert np.abs(F1.cpu().numpy() - Fo).max() <= 1e-4 and np.abs(B1.cpu().numpy() - Bo).max() <= 1e-4
