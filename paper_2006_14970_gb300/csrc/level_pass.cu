@@ -175,6 +175,17 @@ struct Out {
     long long bn_pitch, in_pitch;   // bytes
 };
 
+// Two adjacent 16-bit elements in one 4-byte store (each rounded to nearest even).
+__device__ __forceinline__ void st_pair(__nv_bfloat16 *p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
+__device__ __forceinline__ void st_pair(__half *p, float a, float b) {
+    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+}
+__device__ __forceinline__ void st_pair(float *p, float a, float b) {
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+}
+
 // Compositing epilogue of a lane's pixel pair in row r: In = alpha F + (1 - alpha) Bn.
 template <typename T>
 __device__ __forceinline__ void composite_row(const Out &o, int r, const FB &v, float2 a) {
@@ -202,6 +213,17 @@ __device__ __forceinline__ void store_row(const Out &o, int r, const FB &v, floa
         B2[0] = f2(v.B[0].x, v.B[1].x);
         B2[1] = f2(v.B[2].x, v.B[0].y);
         B2[2] = f2(v.B[1].y, v.B[2].y);
+        return;
+    }
+    if (sizeof(T) == 2 && o.o0 && o.o1 &&
+        (((uint32_t)reinterpret_cast<uintptr_t>(Fr) | (uint32_t)reinterpret_cast<uintptr_t>(Br)) & 3) == 0) {
+        // six 16-bit values per image as three element pairs
+        st_pair(Fr + 0, v.F[0].x, v.F[1].x);
+        st_pair(Fr + 2, v.F[2].x, v.F[0].y);
+        st_pair(Fr + 4, v.F[1].y, v.F[2].y);
+        st_pair(Br + 0, v.B[0].x, v.B[1].x);
+        st_pair(Br + 2, v.B[2].x, v.B[0].y);
+        st_pair(Br + 4, v.B[1].y, v.B[2].y);
         return;
     }
 #pragma unroll
@@ -812,6 +834,18 @@ struct TileSource {
     template <typename U>
     __device__ __forceinline__ float lds(uint32_t a) const {
         return to_f(*reinterpret_cast<const U *>(sm + (a - sbase)));
+    }
+
+    // Two consecutive elements (one 8-byte load for float, one 4-byte for 16 bits).
+    __device__ __forceinline__ float2 lds2(uint32_t a) const {
+        const unsigned char *q = sm + (a - sbase);
+        if (sizeof(T) == 4) return *reinterpret_cast<const float2 *>(q);
+        const uint32_t v = *reinterpret_cast<const uint32_t *>(q);
+        T lo, hi;
+        const unsigned short l16 = (unsigned short)(v & 0xffffu), h16 = (unsigned short)(v >> 16);
+        memcpy(&lo, &l16, sizeof lo);
+        memcpy(&hi, &h16, sizeof hi);
+        return make_float2(to_f(lo), to_f(hi));
     }
 
     __device__ __forceinline__ bool get(const PassArgs &p, const LaneGeo &g, const Ctl &ct, int r,
