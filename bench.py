@@ -196,7 +196,9 @@ def serving_section(fgml, synth, torch, args):
                           torch.from_numpy(s.alpha).to(dt).pin_memory(), w * h))
     # one-at-a-time float32 capacity through the host-buffer entry point
     f32 = [(I.float().pin_memory(), A.float().pin_memory(), n) for I, A, n in templates]
-    for I, A, _ in f32[:2]:
+    # every template once first, so that workspace growth and launch-graph capture are done
+    # before the steady-state capacity is timed
+    for I, A, _ in f32:
         fgml.estimate_host(I, A)
     t0 = time.perf_counter()
     for I, A, _ in f32:
