@@ -139,6 +139,18 @@ fg_status fg_estimate_host(const void *I, const void *alpha, int w, int h, fg_dt
                            const fg_params *params, void *F, void *B, void *stream);
 
 /*
+ * As fg_estimate_host, but returns once the copies and the solve are enqueued on `stream`
+ * (no synchronisation; the paper has no counterpart). For a sequence of images: calls on
+ * two or more streams overlap one image's copy back with the next image's copy in and
+ * solve, since the host link carries both directions at once. The host buffers must stay
+ * valid and unchanged until the stream has passed the call (fg_sync, an event);
+ * page-locked buffers are needed for the copies to run asynchronously. Each stream has its
+ * own staging buffers; calls on one stream run in order.
+ */
+fg_status fg_estimate_host_async(const void *I, const void *alpha, int w, int h, fg_dtype dtype,
+                                 const fg_params *params, void *F, void *B, void *stream);
+
+/*
  * One pass of the level update, for testing a level in isolation:
  * the level is w x h; I_l and alpha_l are the nearest resize of the full-resolution I
  * and alpha (Algorithm 1: resize from the input); the starting F and B are the nearest

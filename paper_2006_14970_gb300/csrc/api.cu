@@ -784,8 +784,15 @@ fg_status fg_estimate_composite(const fg_image *I, const fg_image *alpha, const 
                     (cudaStream_t)stream, &c);
 }
 
-fg_status fg_estimate_host(const void *I, const void *alpha, int w, int h, fg_dtype dtype,
-                           const fg_params *params, void *F, void *B, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// Host buffers in, host buffers out, on `s`: copies of I and alpha into the stream's
+// staging buffers (rows padded to 16 bytes, so the level passes can take the tile path
+// without another copy), the solve, copies of F and B back; `sync` waits for the stream.
+fg_status estimate_host(const void *I, const void *alpha, int w, int h, fg_dtype dtype,
+                        const fg_params *params, void *F, void *B, cudaStream_t s, bool sync) {
     g_err.clear();
     if (!I || !alpha || !F || !B) return fail(FG_ERR_INVALID_ARG, "NULL host pointer");
     if (w < 1 || h < 1 || w > kMaxSide || h > kMaxSide)
@@ -795,26 +802,41 @@ fg_status fg_estimate_host(const void *I, const void *alpha, int w, int h, fg_dt
     const fg_params p = params_or_default(params);
     fg_status st = check_params(p);
     if (st != FG_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
     const int es = elem_size(dtype);
     const size_t n = (size_t)w * h;
-    const size_t bI = (3 * n * es + 255) & ~(size_t)255, bA = (n * es + 255) & ~(size_t)255;
+    const size_t rowI = 3ull * w * es, rowA = (size_t)w * es;
+    const size_t pI = (rowI + 15) & ~(size_t)15, pA = (rowA + 15) & ~(size_t)15;
+    const size_t bI = align256(pI * h), bA = align256(pA * h), bO = align256(3 * n * es);
     Workspace &ws = workspace_for(s);
-    if ((st = ensure(ws.stage, 3 * bI + bA, s)) != FG_OK) return st;
-    char *dI = (char *)ws.stage.p, *dA = dI + bI, *dF = dA + bA, *dB = dF + bI;
+    if ((st = ensure(ws.stage, bI + bA + 2 * bO, s)) != FG_OK) return st;
+    char *dI = (char *)ws.stage.p, *dA = dI + bI, *dF = dA + bA, *dB = dF + bO;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(dI, I, 3 * n * es, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    if ((e = cudaMemcpy2DAsync(dI, pI, I, rowI, rowI, h, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "copy of I to the device");
-    if ((e = cudaMemcpyAsync(dA, alpha, n * es, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    if ((e = cudaMemcpy2DAsync(dA, pA, alpha, rowA, rowA, h, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "copy of alpha to the device");
-    Input in{dI, dA, 3LL * w, (long long)w, w, h};
+    Input in{dI, dA, (long long)(pI / es), (long long)(pA / es), w, h};
     if ((st = estimate(in, (int)dtype, p, dF, dB, 3LL * w, s)) != FG_OK) return st;
     if ((e = cudaMemcpyAsync(F, dF, 3 * n * es, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(e, "copy of F to the host");
     if ((e = cudaMemcpyAsync(B, dB, 3 * n * es, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(e, "copy of B to the host");
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if (sync && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
     return FG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fg_status fg_estimate_host(const void *I, const void *alpha, int w, int h, fg_dtype dtype,
+                           const fg_params *params, void *F, void *B, void *stream) {
+    return estimate_host(I, alpha, w, h, dtype, params, F, B, (cudaStream_t)stream, true);
+}
+
+fg_status fg_estimate_host_async(const void *I, const void *alpha, int w, int h, fg_dtype dtype,
+                                 const fg_params *params, void *F, void *B, void *stream) {
+    return estimate_host(I, alpha, w, h, dtype, params, F, B, (cudaStream_t)stream, false);
 }
 
 fg_status fg_level_pass(const fg_image *I, const fg_image *alpha, const fg_image *F_src,

@@ -71,6 +71,8 @@ def load():
     lib.fg_estimate_host.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      P(Params), vp, vp, vp]
     lib.fg_estimate_host.restype = ctypes.c_int
+    lib.fg_estimate_host_async.argtypes = lib.fg_estimate_host.argtypes
+    lib.fg_estimate_host_async.restype = ctypes.c_int
     lib.fg_level_pass.argtypes = [P(Image), P(Image), P(Image), P(Image), ctypes.c_int,
                                   P(Params), P(Image), P(Image), vp]
     lib.fg_level_pass.restype = ctypes.c_int
@@ -188,6 +190,29 @@ def estimate_host(I: torch.Tensor, alpha: torch.Tensor, p: Params | None = None,
                                    ctypes.byref(p) if p is not None else None,
                                    ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                                    _stream(stream)))
+    return F, B
+
+
+def estimate_host_async(I: torch.Tensor, alpha: torch.Tensor, p: Params | None = None,
+                        F: torch.Tensor | None = None, B: torch.Tensor | None = None, stream=None):
+    """fg_estimate_host_async: as estimate_host, but only enqueued on the stream; the host
+    tensors (pinned) must stay alive and unchanged until the stream has passed it."""
+    if I.is_cuda or alpha.is_cuda:
+        raise ValueError("estimate_host_async takes host tensors")
+    if not (I.is_contiguous() and alpha.is_contiguous()):
+        raise ValueError("I and alpha must be contiguous (they are read after the call returns)")
+    h, w = alpha.shape
+    if I.shape != (h, w, 3) or I.dtype != alpha.dtype or I.dtype not in _DTYPES:
+        raise ValueError("I must be [H, W, 3] and alpha [H, W] of one float dtype")
+    if F is None:
+        F = torch.empty(I.shape, dtype=I.dtype, pin_memory=True)
+    if B is None:
+        B = torch.empty(I.shape, dtype=I.dtype, pin_memory=True)
+    _check(load().fg_estimate_host_async(ctypes.c_void_p(I.data_ptr()),
+                                         ctypes.c_void_p(alpha.data_ptr()), w, h, _DTYPES[I.dtype],
+                                         ctypes.byref(p) if p is not None else None,
+                                         ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                         _stream(stream)))
     return F, B
 
 

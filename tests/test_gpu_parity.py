@@ -208,3 +208,26 @@ def test_packed_rows_off_the_grid_equal_padded_rows(fgml, wh):
     assert torch.equal(F1, F2) and torch.equal(B1, B2)
     Fo, Bo = oracle.ml(s.I, s.alpha)
     assert np.abs(F1.cpu().numpy() - Fo).max() <= 1e-4 and np.abs(B1.cpu().numpy() - Bo).max() <= 1e-4
+
+
+def test_host_entry_points_sync_and_pipelined(fgml):
+    # host buffers in and out: the synchronous call, and a pipelined sequence on two streams
+    # of the asynchronous one, give the device path's bits for every image
+    ss = [synth.make_sample(w, h, 4300 + w) for w, h in ((640, 480), (1023, 767), (333, 1025))]
+    want = []
+    for s in ss:
+        F, B = fgml.estimate(torch.from_numpy(s.I).cuda(), torch.from_numpy(s.alpha).cuda())
+        torch.cuda.synchronize()
+        want.append((F.cpu(), B.cpu()))
+    hs = [(torch.from_numpy(s.I).pin_memory(), torch.from_numpy(s.alpha).pin_memory()) for s in ss]
+    for (I, A), (Fw, Bw) in zip(hs, want):
+        F, B = fgml.estimate_host(I, A)
+        assert torch.equal(F, Fw) and torch.equal(B, Bw)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for k in range(6):
+        I, A = hs[k % 3]
+        outs.append(fgml.estimate_host_async(I, A, stream=streams[k % 2]))
+    torch.cuda.synchronize()
+    for k, (F, B) in enumerate(outs):
+        assert torch.equal(F, want[k % 3][0]) and torch.equal(B, want[k % 3][1])

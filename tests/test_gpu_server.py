@@ -67,15 +67,17 @@ def test_server_results_equal_alone_and_in_mix(fgml):
 
 def test_server_admission_by_memory_budget(fgml):
     jobs = _jobs(10, 2, lo=300, hi=600, dtypes=(torch.float32,))
-    one = max(I.numel() * 4 * 13 // 3 + (1 << 20) for I, _ in jobs)
-    # room for about two jobs at a time: the rest wait in the queue instead of failing
+    need = [I.numel() * 4 * 13 // 3 + (1 << 20) for I, _ in jobs]
+    one = max(need)
+    # room for about two of the largest jobs at a time: the rest wait in the queue
+    # instead of failing (smaller jobs may fit three at a time)
     with fgml.Server(hbm_budget_bytes=int(2.2 * one), streams=2, max_batch=4) as srv:
         tickets = [srv.submit(I, A) for I, A in jobs]
         outs = [srv.wait(t, 60000) for t in tickets]
         st = srv.stats()
     assert st["completed"] == len(jobs) and st["failed"] == 0
     assert st["max_bytes"] <= st["budget_bytes"]
-    assert st["max_inflight"] <= 2
+    assert st["max_inflight"] <= int(2.2 * one) // min(need) < len(jobs)
     for (I, A), (F, B) in zip(jobs, outs):
         Fa, Ba = _alone(fgml, I, A)
         assert float((F - Fa).abs().max()) <= TOL[torch.float32]
