@@ -340,6 +340,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--e2e-streams", type=int, default=2)
     ap.add_argument("--serving-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -440,12 +441,13 @@ def main():
     # link and ~200 MB through HBM, more than L2 holds.
     Ih = torch.from_numpy(s.I).pin_memory()
     Ah = torch.from_numpy(s.alpha).pin_memory()
-    outs = [(torch.empty_like(Ih).pin_memory(), torch.empty_like(Ih).pin_memory()) for _ in range(2)]
-    sts = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ns = max(2, args.e2e_streams)
+    outs = [(torch.empty_like(Ih).pin_memory(), torch.empty_like(Ih).pin_memory()) for _ in range(ns)]
+    sts = [torch.cuda.Stream() for _ in range(ns)]
 
     def host_steps(k):
         for i in range(k):
-            fgml.estimate_host_async(Ih, Ah, None, outs[i % 2][0], outs[i % 2][1], stream=sts[i % 2])
+            fgml.estimate_host_async(Ih, Ah, None, outs[i % ns][0], outs[i % ns][1], stream=sts[i % ns])
 
     host_steps(2 * args.warmup)
     barrier()
@@ -453,11 +455,13 @@ def main():
     e_start = torch.cuda.Event(enable_timing=True)
     e_end = torch.cuda.Event(enable_timing=True)
     e_start.record(sts[0])
-    sts[1].wait_event(e_start)
+    for st in sts[1:]:
+        st.wait_event(e_start)
     host_steps(n_e2e)
-    e_side = torch.cuda.Event()
-    e_side.record(sts[1])
-    sts[0].wait_event(e_side)
+    for st in sts[1:]:
+        e_side = torch.cuda.Event()
+        e_side.record(st)
+        sts[0].wait_event(e_side)
     e_end.record(sts[0])
     e_end.synchronize()
     ms_e2e = max_over_ranks(e_start.elapsed_time(e_end)) / n_e2e
@@ -467,7 +471,7 @@ def main():
     e2e = {"value": replica_throughput(world, w * h, ms_e2e), "unit": "Mpix/s",
            "h2d_bytes_per_step": int(Ih.numel() * 4 + Ah.numel() * 4),
            "d2h_bytes_per_step": int(2 * Ih.numel() * 4), "ms_per_step": ms_e2e,
-           "steps": n_e2e, "how": "fg_estimate_host_async on two streams, pinned host buffers",
+           "steps": n_e2e, "how": f"fg_estimate_host_async on {ns} streams, pinned host buffers",
            "one_call_at_a_time": {"value": replica_throughput(world, w * h, ms_e2e_1),
                                   "ms_per_step": ms_e2e_1}}
 
