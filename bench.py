@@ -340,7 +340,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
-    ap.add_argument("--e2e-streams", type=int, default=2)
+    ap.add_argument("--e2e-streams", type=int, default=3)
     ap.add_argument("--serving-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -435,7 +435,7 @@ def main():
     value = replica_throughput(world, w * h, ms)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed
-    # region: a sequence of images on two streams (fg_estimate_host_async), so one image's
+    # region: a sequence of images on several streams (fg_estimate_host_async), so one image's
     # copy back overlaps the next one's copy in and solve; every step still copies its own
     # inputs in and its F and B out. No L2 flush: every step streams 126 MB over the host
     # link and ~200 MB through HBM, more than L2 holds.
