@@ -167,6 +167,8 @@ def batch_section(fgml, synth, torch, dev, timed, world, args):
     outs = [(torch.empty_like(I), torch.empty_like(I)) for I, _ in imgs]
     npx = sum(s.alpha.size for s in ss)
     steps = max(3, args.steps // 4)
+    # the work list's strip shape is chosen by measurement on this batch first
+    chosen, tune_ms = fgml.autotune_batch(imgs, None, outs)
     ms_b = timed(lambda: fgml.estimate_batch(imgs, None, outs), steps, args.warmup)
 
     def one_by_one():
@@ -177,7 +179,11 @@ def batch_section(fgml, synth, torch, dev, timed, world, args):
             "value": world * npx / (ms_b * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms_b,
             "one_at_a_time": {"value": world * npx / (ms_1 * 1e-3) / 1e6, "unit": "Mpix/s",
                               "ms_per_step": ms_1},
-            "launches_per_step": 2}
+            # coarse levels, work list, and the row-aligned copy when some rows are off the
+            # 16-byte grid
+            "launches_per_step": 2 + int(any((3 * s.alpha.shape[1] * 4) % 16 for s in ss)),
+            "strip_shape_candidate": chosen,
+            "autotune_ms_per_call": tune_ms}
 
 
 def serving_section(fgml, synth, torch, args):

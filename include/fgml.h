@@ -205,6 +205,20 @@ fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image *alpha,
                             const fg_params *params, fg_image *F, fg_image *B, void *stream);
 
 /*
+ * Chooses the strip shape of fg_estimate_batch's work list by measurement (the paper has
+ * no counterpart): runs the given batch once per candidate shape (a handful of
+ * strips-per-SM / rows-per-strip settings), times two calls of each with events on
+ * `stream`, and keeps the fastest as the process-wide setting of later batches (results do
+ * not depend on it: every strip computes the same per-pixel updates). Arguments as
+ * fg_estimate_batch (F and B are overwritten). *chosen (may be NULL): index of the chosen
+ * candidate; *ms (may be NULL): its time per call. Synchronous. The environment variable
+ * FGML_BATCH_STRIPS="per_sm,lo,hi" sets the starting shape instead.
+ */
+fg_status fg_autotune_batch(int n, const fg_image *I, const fg_image *alpha,
+                            const fg_params *params, fg_image *F, fg_image *B, void *stream,
+                            int *chosen, float *ms);
+
+/*
  * Diagnostic of the device-side bounded waits (not part of the method): runs the work-list
  * kernel on one item that waits for a count nothing ever reaches, with a 20 ms bound, and
  * checks that the kernel gives up, reports it through the device error word and leaves

@@ -1192,31 +1192,34 @@ static_assert(kRingSlots * kBatchRingSlotCap <= kBatchRegionCap, "ring slots exc
 constexpr long long kBatchWaitNs = 2000000000; // bound of one dependency wait (2 s)
 
 // Rows per strip of a batch pass: a few waves of the persistent grid per level.
-// Rows per strip of a work-list pass: about `per_sm` strips per SM for the level, within
-// [lo, hi] rows (FGML_BATCH_STRIPS="per_sm,lo,hi" overrides the defaults for tuning).
+// Strip shape of the work-list passes: about `per_sm` strips per SM for a level, within
+// [lo, hi] rows. The default comes from FGML_BATCH_STRIPS="per_sm,lo,hi" or the built-in
+// {4, 8, 64}; fg_autotune_batch replaces it with the fastest measured candidate.
+struct BatchStrips {
+    int per_sm, lo, hi;
+};
+constexpr BatchStrips kStripCandidates[] = {{4, 8, 64}, {2, 16, 128}, {8, 8, 64}, {4, 16, 96},
+                                            {2, 8, 48}, {6, 8, 64}};
+std::mutex g_strips_mu;
+BatchStrips g_strips = [] {
+    BatchStrips v = kStripCandidates[0];
+    const char *e = std::getenv("FGML_BATCH_STRIPS");
+    int a, b, c;
+    if (e && std::sscanf(e, "%d,%d,%d", &a, &b, &c) == 3 && a > 0 && b > 0 && c >= b) v = {a, b, c};
+    return v;
+}();
+
 int batch_strip_rows(int w, int h) {
-    static const int cfg[3] = {4, 8, 64};
-    static int v[3] = {0, 0, 0};
-    static bool init = false;
-    if (!init) {
-        v[0] = cfg[0];
-        v[1] = cfg[1];
-        v[2] = cfg[2];
-        const char *e = std::getenv("FGML_BATCH_STRIPS");
-        int a, b, c;
-        if (e && std::sscanf(e, "%d,%d,%d", &a, &b, &c) == 3 && a > 0 && b > 0 && c >= b) {
-            v[0] = a;
-            v[1] = b;
-            v[2] = c;
-        }
-        init = true;
+    BatchStrips v;
+    {
+        std::lock_guard<std::mutex> lk(g_strips_mu);
+        v = g_strips;
     }
     const int nx = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
-    const long long target = (long long)sm_count() * v[0];
+    const long long target = (long long)sm_count() * v.per_sm;
     long long r = ((long long)h * nx + target - 1) / target;
-    return (int)std::min<long long>(std::max<long long>(r, v[1]), v[2]);
+    return (int)std::min<long long>(std::max<long long>(r, v.lo), v.hi);
 }
-
 
 PassArgs batch_pass_args(int dtype, const fg_params &p, const Input &in, const State &src,
                          void *Fd, void *Bd, long long d_pitch, int w, int h, bool *ring) {
@@ -1543,6 +1546,61 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
     b.region = (std::max(kRingSlots * slot_max, tile_max) + 127) & ~127;
     if (b.region > kBatchRegionCap) return fail(FG_ERR_CUDA, "batch region %d exceeds the cap", b.region);
     return batch_launch(dtype, p.clamp, b, s);
+}
+
+extern "C" fg_status fg_autotune_batch(int n, const fg_image *I, const fg_image *alpha,
+                                       const fg_params *params, fg_image *F, fg_image *B,
+                                       void *stream, int *chosen, float *ms) {
+    g_err.clear();
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nc = (int)(sizeof kStripCandidates / sizeof kStripCandidates[0]);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "autotune events");
+    }
+    BatchStrips keep;
+    {
+        std::lock_guard<std::mutex> lk(g_strips_mu);
+        keep = g_strips;
+    }
+    int best = -1;
+    float best_ms = 0.f;
+    fg_status st = FG_OK;
+    for (int c = 0; c < nc && st == FG_OK; ++c) {
+        {
+            std::lock_guard<std::mutex> lk(g_strips_mu);
+            g_strips = kStripCandidates[c];
+        }
+        // one untimed call (workspace growth), then two timed ones
+        st = fg_estimate_batch(n, I, alpha, params, F, B, stream);
+        if (st != FG_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 2 && st == FG_OK; ++r) st = fg_estimate_batch(n, I, alpha, params, F, B, stream);
+        if (st != FG_OK) break;
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "autotune timing");
+            break;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (best < 0 || t < best_ms) {
+            best = c;
+            best_ms = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_strips_mu);
+        g_strips = st == FG_OK && best >= 0 ? kStripCandidates[best] : keep;
+    }
+    if (st != FG_OK) return st;
+    if (chosen) *chosen = best;
+    if (ms) *ms = best_ms / 2;
+    return FG_OK;
 }
 
 extern "C" fg_status fg_selftest_bounded_wait(void *stream) {

@@ -79,6 +79,9 @@ def load():
     lib.fg_estimate_batch.argtypes = [ctypes.c_int, P(Image), P(Image), P(Params), P(Image),
                                       P(Image), vp]
     lib.fg_estimate_batch.restype = ctypes.c_int
+    lib.fg_autotune_batch.argtypes = [ctypes.c_int, P(Image), P(Image), P(Params), P(Image),
+                                      P(Image), vp, P(ctypes.c_int), P(ctypes.c_float)]
+    lib.fg_autotune_batch.restype = ctypes.c_int
     lib.fg_selftest_bounded_wait.argtypes = [vp]
     lib.fg_selftest_bounded_wait.restype = ctypes.c_int
     lib.fg_sync.argtypes = [vp]
@@ -248,6 +251,25 @@ def estimate_batch(images, p: Params | None = None, outputs=None, stream=None):
     _check(load().fg_estimate_batch(n, iI, iA, ctypes.byref(p) if p is not None else None,
                                     iF, iB, _stream(stream)))
     return outputs
+
+
+def autotune_batch(images, p: Params | None = None, outputs=None, stream=None):
+    """fg_autotune_batch on a list of (I, alpha) device tensor pairs: picks the work-list
+    strip shape by measurement; returns (candidate index, ms per call)."""
+    n = len(images)
+    if outputs is None:
+        outputs = [(torch.empty_like(I, memory_format=torch.contiguous_format),
+                    torch.empty_like(I, memory_format=torch.contiguous_format)) for I, _ in images]
+    arr = Image * n
+    iI = arr(*[_image(I, 3, "I") for I, _ in images])
+    iA = arr(*[_image(A, 1, "alpha") for _, A in images])
+    iF = arr(*[_image(F, 3, "F") for F, _ in outputs])
+    iB = arr(*[_image(B, 3, "B") for _, B in outputs])
+    chosen = ctypes.c_int(-1)
+    ms = ctypes.c_float(0.0)
+    _check(load().fg_autotune_batch(n, iI, iA, ctypes.byref(p) if p is not None else None, iF, iB,
+                                    _stream(stream), ctypes.byref(chosen), ctypes.byref(ms)))
+    return chosen.value, ms.value
 
 
 def selftest_bounded_wait(stream=None) -> int:

@@ -107,3 +107,16 @@ def test_bounded_wait_gives_up_and_context_survives(fgml):
     fgml.sync()
     Fo, Bo = oracle.ml(s.I, s.alpha)
     assert np.abs(F.cpu().numpy() - Fo).max() <= TOL
+
+
+def test_autotune_picks_a_strip_shape_and_results_do_not_change(fgml):
+    ss = _samples([(300, 211), (1024, 768), (77, 900), (640, 480)], 1000)
+    imgs = [(_dev(s.I), _dev(s.alpha)) for s in ss]
+    before = fgml.estimate_batch(imgs)
+    fgml.sync()
+    chosen, ms = fgml.autotune_batch(imgs)
+    assert 0 <= chosen < 6 and ms > 0
+    after = fgml.estimate_batch(imgs)
+    fgml.sync()
+    for (F0, B0), (F1, B1) in zip(before, after):
+        assert torch.equal(F0, F1) and torch.equal(B0, B1)
