@@ -155,8 +155,20 @@ def cpu_baseline(sample: str, seconds: float = 10.0):
         dt = time.perf_counter() - t0
         if dt >= seconds or n >= 50:
             break
-    return {"value": n * w * h / dt / 1e6, "unit": "Mpix/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n} full FP64 solves of the {w}x{h} workload image ({dt:.1f} s)"}
+    out = {"value": n * w * h / dt / 1e6, "unit": "Mpix/s", "cores": threads, "kind": "oracle",
+           "sample": f"{n} full FP64 solves of the {w}x{h} workload image ({dt:.1f} s)"}
+    # the paper times its method single-threaded: the oracle on one core, best of 3
+    oracle.set_threads(1)
+    best = None
+    for _ in range(3):
+        t1 = time.perf_counter()
+        oracle.ml(s.I, s.alpha)
+        d1 = time.perf_counter() - t1
+        best = d1 if best is None else min(best, d1)
+    oracle.set_threads(threads)
+    out["single_thread"] = {"value": w * h / best / 1e6, "unit": "Mpix/s", "cores": 1,
+                            "sample": f"best of 3 FP64 solves of the {w}x{h} image ({best:.2f} s each)"}
+    return out
 
 
 def batch_section(fgml, synth, torch, dev, timed, world, args):
