@@ -7,8 +7,10 @@
 //    which arrive while the small levels run.
 //  - F and B live in shared memory as (F, B) pairs per channel, ping-ponged between two
 //    buffers, with one barrier per Jacobi sweep over the warps that hold the level.
-//  - Levels of at most 64 pixels run one thread per (pixel, channel), so a sweep is a
-//    short dependent chain per thread; larger levels run one thread per pixel.
+//  - Levels of at most 64 pixels run in three warps, one per channel, with each pixel's
+//    (F, B) in registers and the neighbours taken by warp shuffles: a sweep is a short
+//    dependent chain without shared memory or barriers. Larger levels run one thread per
+//    pixel with (F, B) in shared memory.
 //  - Each thread forms its pixel's neighbour weights and the inverse of its 2x2 matrix
 //    (Section III-C) once per level; a sweep is then 4 neighbour reads, packed
 //    multiply-adds and the clamped solve (Algorithm 1).
@@ -20,7 +22,8 @@ namespace fgml {
 namespace {
 
 constexpr int kThreads = 1024;
-constexpr int kSplitMax = 64;   // levels up to this many pixels run one thread per (pixel, channel)
+constexpr int kSplitMax = 64;   // levels up to this many pixels run in registers, one warp per channel
+constexpr unsigned kFull32 = 0xffffffffu;
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 
@@ -139,21 +142,115 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs &p) {
             rest_waited = true;
         }
         __syncthreads();   // the previous level (and the gathered inputs) are visible
-        const int nact = split ? 3 * n : n;        // active threads
-        const int nt = (nact + 31) & ~31;          // threads taking part in the barriers
+        if (split) {
+            // up to 64 pixels: warp c holds channel c of every pixel in registers (pixels
+            // lane and lane + 32) and takes its neighbours by shuffles; the channels are
+            // independent given the weights, so no barrier is needed between sweeps
+            if (tid < 3 * 32) {
+                const int c = tid >> 5, lane = tid & 31;
+                const float2 *src = buf + cur * 3 * kCoarseCap + c * kCoarseCap;
+                float2 *dst = buf + (cur ^ 1) * 3 * kCoarseCap + c * kCoarseCap;
+                const bool two = n > 32;
+                float2 v[2];
+                int nb[2][4];
+                float wj[2][4], ai[2], be[2], mFF[2], mBB[2], nFB[2], Ic[2];
+                bool mine[2], red[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int i = lane + 32 * u;
+                    mine[u] = i < n;
+                    const int ii = mine[u] ? i : 0;
+                    const int x = ii % w, y = ii / w;
+                    red[u] = ((x + y) & 1) == 0;
+                    // starting F, B: nearest resize of the previous level
+                    v[u] = src[nearest_src(y, ph, h) * pw + nearest_src(x, pw, w)];
+                    nb[u][0] = y * w + max(x - 1, 0);
+                    nb[u][1] = y * w + min(x + 1, w - 1);
+                    nb[u][2] = max(y - 1, 0) * w + x;
+                    nb[u][3] = min(y + 1, h - 1) * w + x;
+                    ai[u] = Alv[o + ii];
+                    be[u] = 1.f - ai[u];
+                    float S = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        wj[u][j] = fmaf(p.omega, fabsf(ai[u] - Alv[o + nb[u][j]]), p.eps);
+                        S += wj[u][j];
+                    }
+                    const float A00 = fmaf(ai[u], ai[u], S), A11 = fmaf(be[u], be[u], S);
+                    const float A01 = ai[u] * be[u];
+                    const float m = __fdividef(1.f, fmaf(A00, A11, -A01 * A01));
+                    mFF[u] = A11 * m;
+                    mBB[u] = A00 * m;
+                    nFB[u] = -A01 * m;
+                    Ic[u] = Ilv[3 * (o + ii) + c];
+                }
+                // the (F, B) of pixel j, held by lane j % 32 in slot j / 32
+                auto fetch = [&](int j) {
+                    float2 a;
+                    a.x = __shfl_sync(kFull32, v[0].x, j & 31);
+                    a.y = __shfl_sync(kFull32, v[0].y, j & 31);
+                    if (two) {
+                        float2 b;
+                        b.x = __shfl_sync(kFull32, v[1].x, j & 31);
+                        b.y = __shfl_sync(kFull32, v[1].y, j & 31);
+                        if (j >= 32) a = b;
+                    }
+                    return a;
+                };
+                auto solve = [&](int u) {
+                    float2 sv = __fmul2_rn(f2(wj[u][0], wj[u][0]), fetch(nb[u][0]));
+#pragma unroll
+                    for (int j = 1; j < 4; ++j) sv = __ffma2_rn(f2(wj[u][j], wj[u][j]), fetch(nb[u][j]), sv);
+                    const float bF = fmaf(ai[u], Ic[u], sv.x), bB = fmaf(be[u], Ic[u], sv.y);
+                    float gF = fmaf(mFF[u], bF, nFB[u] * bB);
+                    float gB = fmaf(mBB[u], bB, nFB[u] * bF);
+                    if (CLAMP) {
+                        gF = __saturatef(gF);
+                        gB = __saturatef(gB);
+                    }
+                    return f2(gF, gB);
+                };
+                const int rounds = p.order == 1 ? 2 * k : k;
+                for (int it = 0; it < rounds; ++it) {
+                    // Jacobi: every pixel from the previous values; red-black: one colour
+                    // per round, the other keeps its value
+                    // every lane of the warp computes (the shuffles need them all), then
+                    // keeps the solution only where its pixel is updated this round
+                    float2 nv[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const bool upd = p.order != 1 || red[u] == ((it & 1) == 0);
+                        nv[u] = v[u];
+                        if (u == 0 || two) {
+                            const float2 sol = solve(u);
+                            if (upd) nv[u] = sol;
+                        }
+                    }
+                    v[0] = nv[0];
+                    v[1] = nv[1];
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (mine[u]) dst[lane + 32 * u] = v[u];
+            }
+            cur ^= 1;
+            pw = w;
+            ph = h;
+            continue;
+        }
+        const int nt = (n + 31) & ~31;             // threads taking part in the barriers
         if (tid < nt) {
-            const bool mine = tid < nact;
-            // split levels: thread = (channel c, pixel i); else thread = pixel i, all channels
-            const int c0 = split && mine ? tid / n : 0;
-            const int i = mine ? tid - c0 * n : 0;
+            // thread = pixel i, all three channels
+            const bool mine = tid < n;
+            const int i = mine ? tid : 0;
             const int x = i % w, y = i / w;
-            const int nc = split ? 1 : 3;
             float2 *src = buf + cur * 3 * kCoarseCap;
             float2 *dst = buf + (cur ^ 1) * 3 * kCoarseCap;
             // starting F, B: nearest resize of the previous level
             if (mine) {
                 const int q = nearest_src(y, ph, h) * pw + nearest_src(x, pw, w);
-                for (int c = c0; c < c0 + nc; ++c) dst[c * kCoarseCap + i] = src[c * kCoarseCap + q];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) dst[c * kCoarseCap + i] = src[c * kCoarseCap + q];
             }
             // neighbours clamped onto the level (Algorithm 1), their weights and A^{-1}
             int nb[4];
@@ -173,7 +270,7 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs &p) {
             const float mFF = A11 * m, mBB = A00 * m, nFB = -A01 * m;
             float Ic[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) Ic[c] = Ilv[3 * (o + i) + (split ? c0 : c)];
+            for (int c = 0; c < 3; ++c) Ic[c] = Ilv[3 * (o + i) + c];
             cur ^= 1;
             level_sync(nt);
 
@@ -190,39 +287,19 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs &p) {
             if (p.order == 1) {
                 // red-black: per iteration the x + y even pixels, then the odd ones, each
                 // colour in place (it reads only the other colour, or itself at a border)
-                const int cb = split ? c0 * kCoarseCap : 0;
                 const bool on0 = mine && ((x + y) & 1) == 0, on1 = mine && ((x + y) & 1) == 1;
-                float2 *st = buf + cur * 3 * kCoarseCap + cb;
+                float2 *st = buf + cur * 3 * kCoarseCap;
                 for (int it = 0; it < 2 * k; ++it) {
                     if ((it & 1) ? on1 : on0) {
-                        auto one = [&](int c) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
                             float2 sv = __fmul2_rn(f2(wj[0], wj[0]), st[c * kCoarseCap + nb[0]]);
 #pragma unroll
                             for (int j = 1; j < 4; ++j)
                                 sv = __ffma2_rn(f2(wj[j], wj[j]), st[c * kCoarseCap + nb[j]], sv);
                             st[c * kCoarseCap + i] = solve(sv, Ic[c]);
-                        };
-                        if (split) {
-                            one(0);
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) one(c);
                         }
                     }
-                    level_sync(nt);
-                }
-            } else if (split) {
-                const int cb = c0 * kCoarseCap;
-                for (int it = 0; it < k; ++it) {
-                    const float2 *s2 = buf + cur * 3 * kCoarseCap + cb;
-                    float2 *d2 = buf + (cur ^ 1) * 3 * kCoarseCap + cb;
-                    if (mine) {
-                        float2 sv = __fmul2_rn(f2(wj[0], wj[0]), s2[nb[0]]);
-#pragma unroll
-                        for (int j = 1; j < 4; ++j) sv = __ffma2_rn(f2(wj[j], wj[j]), s2[nb[j]], sv);
-                        d2[i] = solve(sv, Ic[0]);
-                    }
-                    cur ^= 1;
                     level_sync(nt);
                 }
             } else {
