@@ -40,7 +40,7 @@ typedef enum {
     FG_ERR_OOM = 2,           /* workspace allocation failed */
     FG_ERR_CUDA = 3,          /* a CUDA runtime call failed; see fg_last_error() */
     FG_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
-    FG_ERR_RANGE = 5,         /* input outside [0, 1] or NaN (only when checked) */
+    FG_ERR_RANGE = 5,         /* input outside [0, 1] or NaN (only when FGML_DEBUG=1) */
     FG_ERR_BUSY = 6,          /* a resource is in use (server full, etc.) */
     FG_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
 } fg_status;
@@ -105,10 +105,14 @@ int fg_schedule(int w, int h, const fg_params *p, int *ws, int *hs, int *ks, int
  *  F, B:  device, w x h x 3 outputs, same dtype; must not overlap the inputs.
  *  params: NULL for the paper's defaults.
  *  stream: cudaStream_t (NULL = default stream). Asynchronous.
- * Update order: Jacobi. Levels whose F/B fit in one SM's shared memory run in one
- * persistent block; each larger level runs as one pass (two sweeps fused) through HBM.
+ * Update order: params->order (Jacobi by default). Levels whose F/B fit in one SM's shared
+ * memory run in one persistent block; each larger level runs as one pass (two sweeps fused)
+ * through HBM. Inputs are not validated on this path; with the environment variable
+ * FGML_DEBUG=1 the call first checks that I and alpha are in [0, 1] without NaN
+ * (synchronising the stream) and returns FG_ERR_RANGE otherwise. Large inputs whose rows
+ * are not on the 16-byte grid are copied once into a row-aligned workspace copy.
  * Errors: FG_ERR_INVALID_ARG for bad images/params, FG_ERR_OOM if the workspace cannot
- * be allocated, FG_ERR_CUDA for a failed launch.
+ * be allocated, FG_ERR_CUDA for a failed launch, FG_ERR_RANGE (checked inputs only).
  */
 fg_status fg_estimate(const fg_image *I, const fg_image *alpha, const fg_params *params,
                       fg_image *F, fg_image *B, void *stream);

@@ -151,6 +151,7 @@ struct Workspace {
     Buf batch;    // work lists and per-image levels of fg_estimate_batch
     Buf aux;      // per-block partial sums of fg_quality
     Buf cg;       // vectors of fg_minimiser_cg
+    Buf check;    // counter of the optional input range check
     Buf align;    // copies of I and alpha with rows on the 16-byte grid (tensor maps need it)
     // launch sequences of fg_estimate captured as CUDA graphs, by call signature
     std::map<std::string, cudaGraphExec_t> graphs;
@@ -679,6 +680,25 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
     return FG_OK;
 }
 
+// FGML_DEBUG=1: every solve first checks that I and alpha hold values in [0, 1] (no NaN)
+// and returns FG_ERR_RANGE otherwise. The check synchronises the stream.
+fg_status check_inputs(const Input &in, int dtype, cudaStream_t s) {
+    const char *v = std::getenv("FGML_DEBUG");
+    if (!(v && *v && *v != '0')) return FG_OK;
+    Workspace &ws = workspace_for(s);
+    fg_status st = ensure(ws.check, sizeof(unsigned long long), s);
+    if (st != FG_OK) return st;
+    unsigned long long *bad = static_cast<unsigned long long *>(ws.check.p), h = 0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof h, s);
+    if (e == cudaSuccess) e = launch_range_check(dtype, in.I, in.I_pitch, in.w, in.h, 3, bad, s);
+    if (e == cudaSuccess) e = launch_range_check(dtype, in.A, in.A_pitch, in.w, in.h, 1, bad, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, bad, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "input range check");
+    if (h) return fail(FG_ERR_RANGE, "%llu values of I and alpha are outside [0, 1] or NaN", h);
+    return FG_OK;
+}
+
 fg_params params_or_default(const fg_params *p) {
     fg_params d;
     fg_params_default(&d);
@@ -738,6 +758,7 @@ fg_status fg_estimate(const fg_image *I, const fg_image *alpha, const fg_params 
         return fail(FG_ERR_INVALID_ARG, "outputs overlap each other or the inputs");
     const int es = elem_size(I->dtype);
     Input in{I->ptr, alpha->ptr, I->row_pitch_bytes / es, alpha->row_pitch_bytes / es, I->w, I->h};
+    if ((st = check_inputs(in, (int)I->dtype, (cudaStream_t)stream)) != FG_OK) return st;
     return estimate(in, (int)I->dtype, p, F->ptr, B->ptr, F->row_pitch_bytes / es,
                     (cudaStream_t)stream);
 }
@@ -775,6 +796,7 @@ fg_status fg_estimate_composite(const fg_image *I, const fg_image *alpha, const 
         return fail(FG_ERR_INVALID_ARG, "outputs overlap each other or the inputs");
     const int es = elem_size(I->dtype);
     Input in{I->ptr, alpha->ptr, I->row_pitch_bytes / es, alpha->row_pitch_bytes / es, I->w, I->h};
+    if ((st = check_inputs(in, (int)I->dtype, (cudaStream_t)stream)) != FG_OK) return st;
     Composite c;
     c.Bn = B_new->ptr;
     c.In = I_new->ptr;
@@ -1035,6 +1057,7 @@ fg_status fg_release_workspace(void *stream) {
     cudaFree(w.batch.p);
     cudaFree(w.aux.p);
     cudaFree(w.cg.p);
+    cudaFree(w.check.p);
     cudaFree(w.align.p);
     return FG_OK;
 }

@@ -130,6 +130,11 @@ struct StageList {
 cudaError_t launch_stage_rows(int dtype, const StageList &list, int njobs, long long total_rows,
                               cudaStream_t s);
 
+// Adds to *bad (device) the number of values of a w x h x ch image (pitch in elements)
+// outside [0, 1] or NaN (the optional input check).
+cudaError_t launch_range_check(int dtype, const void *p, long long pitch, int w, int h, int ch,
+                               unsigned long long *bad, cudaStream_t s);
+
 // Tile chunks in flight per warp in the work-list kernel.
 constexpr int kBatchTileSlots = 3;
 size_t level_batch_smem(int region);

@@ -73,3 +73,38 @@ cudaError_t launch_stage_rows(int dtype, const StageList &list, int njobs, long 
 }
 
 }  // namespace fgml
+
+namespace fgml {
+namespace {
+
+// Counts the values of a w x h x ch image outside [0, 1] (NaN included) into *bad.
+template <typename T>
+__global__ void __launch_bounds__(256) range_check_kernel(const T *p, long long pitch, int w, int h,
+                                                          int ch, unsigned long long *bad) {
+    const long long row = (long long)w * ch;
+    unsigned long long mine = 0;
+    for (long long y = blockIdx.x; y < h; y += gridDim.x)
+        for (long long x = threadIdx.x; x < row; x += blockDim.x) {
+            const float v = ld_elem(p + y * pitch + x);
+            if (!(v >= 0.f && v <= 1.f)) ++mine;
+        }
+    if (mine) atomicAdd(bad, mine);
+}
+
+}  // namespace
+
+cudaError_t launch_range_check(int dtype, const void *p, long long pitch, int w, int h, int ch,
+                               unsigned long long *bad, cudaStream_t s) {
+    const int grid = std::max(1, std::min(h, 1216));
+    switch (dtype) {
+        case kF32: range_check_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(p), pitch, w, h, ch, bad); break;
+        case kBF16:
+            range_check_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(p), pitch, w, h, ch, bad);
+            break;
+        case kF16: range_check_kernel<__half><<<grid, 256, 0, s>>>(static_cast<const __half *>(p), pitch, w, h, ch, bad); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fgml

@@ -231,3 +231,23 @@ def test_host_entry_points_sync_and_pipelined(fgml):
     torch.cuda.synchronize()
     for k, (F, B) in enumerate(outs):
         assert torch.equal(F, want[k % 3][0]) and torch.equal(B, want[k % 3][1])
+
+
+def test_debug_input_range_check(fgml, monkeypatch):
+    s = synth.make_sample(64, 48, 4400)
+    I = torch.from_numpy(s.I).cuda()
+    A = torch.from_numpy(s.alpha).cuda()
+    nan_I = I.clone()
+    nan_I[3, 5, 1] = float("nan")
+    big_A = A.clone()
+    big_A[0, 0] = 1.5
+    monkeypatch.setenv("FGML_DEBUG", "1")
+    for bi, ba in ((nan_I, A), (I, big_A)):
+        with pytest.raises(fgml.FgmlError) as e:
+            fgml.estimate(bi, ba)
+        assert e.value.status == fgml.FG_ERR_RANGE
+    F, B = fgml.estimate(I, A)
+    torch.cuda.synchronize()
+    monkeypatch.delenv("FGML_DEBUG")
+    fgml.estimate(nan_I, A)      # unchecked: the call itself succeeds
+    torch.cuda.synchronize()
