@@ -216,7 +216,9 @@ fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image *alpha,
  * not depend on it: every strip computes the same per-pixel updates). Arguments as
  * fg_estimate_batch (F and B are overwritten). *chosen (may be NULL): index of the chosen
  * candidate; *ms (may be NULL): its time per call. Synchronous. The environment variable
- * FGML_BATCH_STRIPS="per_sm,lo,hi" sets the starting shape instead.
+ * FGML_BATCH_STRIPS="per_sm,lo,hi" sets the starting shape instead; with
+ * FGML_TUNE_CACHE=path the chosen shape is also written to that file (one line per GPU
+ * model) and later processes start from it.
  */
 fg_status fg_autotune_batch(int n, const fg_image *I, const fg_image *alpha,
                             const fg_params *params, fg_image *F, fg_image *B, void *stream,

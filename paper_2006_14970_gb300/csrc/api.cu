@@ -3,6 +3,8 @@
 #include "fgml.h"
 #include "fgml_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -136,6 +138,14 @@ bool overlap(const fg_image *a, int ca, const fg_image *b, int cb) {
     return x.first < y.second && y.first < x.second;
 }
 
+// NVTX range over one entry point (shows in profilers' timelines; a no-op without a tool).
+struct Range {
+    explicit Range(const char *m) { nvtxRangePushA(m); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+
 // ------------------------------------------------------------------ workspaces
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -182,6 +192,9 @@ Workspace &workspace_for(cudaStream_t s) {
 
 fg_status ensure(Buf &b, size_t need, cudaStream_t s) {
     if (b.bytes >= need) return FG_OK;
+    // host-side fault injection for tests: FGML_FAIL_ALLOC=1 refuses workspace growth
+    if (const char *f = std::getenv("FGML_FAIL_ALLOC"))
+        if (*f && *f != '0') return fail(FG_ERR_OOM, "workspace allocation of %zu bytes refused (FGML_FAIL_ALLOC)", need);
     if (b.p) {
         cudaStreamSynchronize(s);   // the old buffer may still be read by queued work
         cudaFree(b.p);
@@ -739,6 +752,7 @@ int fg_schedule(int w, int h, const fg_params *params, int *ws, int *hs, int *ks
 fg_status fg_estimate(const fg_image *I, const fg_image *alpha, const fg_params *params,
                       fg_image *F, fg_image *B, void *stream) {
     g_err.clear();
+    Range range("fg_estimate");
     fg_status st;
     if ((st = check_image(I, 3, "I")) != FG_OK) return st;
     if ((st = check_image(alpha, 1, "alpha")) != FG_OK) return st;
@@ -767,6 +781,7 @@ fg_status fg_estimate_composite(const fg_image *I, const fg_image *alpha, const 
                                 fg_image *F, fg_image *B, const fg_image *B_new, fg_image *I_new,
                                 void *stream) {
     g_err.clear();
+    Range range("fg_estimate_composite");
     fg_status st;
     if ((st = check_image(B_new, 3, "B_new")) != FG_OK) return st;
     if ((st = check_image(I_new, 3, "I_new")) != FG_OK) return st;
@@ -816,6 +831,7 @@ namespace {
 fg_status estimate_host(const void *I, const void *alpha, int w, int h, fg_dtype dtype,
                         const fg_params *params, void *F, void *B, cudaStream_t s, bool sync) {
     g_err.clear();
+    Range range("fg_estimate_host");
     if (!I || !alpha || !F || !B) return fail(FG_ERR_INVALID_ARG, "NULL host pointer");
     if (w < 1 || h < 1 || w > kMaxSide || h > kMaxSide)
         return fail(FG_ERR_INVALID_ARG, "size %dx%d outside [1, %d]", w, h, kMaxSide);
@@ -908,6 +924,7 @@ fg_status fg_level_pass(const fg_image *I, const fg_image *alpha, const fg_image
 fg_status fg_quality(const fg_image *F_est, const fg_image *F_gt, const fg_image *alpha_gt,
                      double *out, void *stream) {
     g_err.clear();
+    Range range("fg_quality");
     fg_status st;
     if ((st = check_image(F_est, 3, "F_est")) != FG_OK) return st;
     if ((st = check_image(F_gt, 3, "F_gt")) != FG_OK) return st;
@@ -957,6 +974,7 @@ fg_status fg_minimiser_cg(const fg_image *I, const fg_image *alpha, const fg_par
                           double *F, double *B, int max_iters, double rel_tol, int *iters,
                           double *rel_residual, void *stream) {
     g_err.clear();
+    Range range("fg_minimiser_cg");
     fg_status st;
     if ((st = check_image(I, 3, "I")) != FG_OK) return st;
     if ((st = check_image(alpha, 1, "alpha")) != FG_OK) return st;
@@ -1232,10 +1250,61 @@ BatchStrips g_strips = [] {
     return v;
 }();
 
+// FGML_TUNE_CACHE=path keeps the autotuned strip shape per GPU model across processes:
+// one line per model, "<device name>\t<per_sm>,<lo>,<hi>".
+std::string device_name() {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, current_device()) != cudaSuccess) return "unknown";
+    return prop.name;
+}
+
+bool g_strips_cache_read = false;
+
+void read_tune_cache() {   // with g_strips_mu held
+    g_strips_cache_read = true;
+    const char *path = std::getenv("FGML_TUNE_CACHE");
+    if (!path || !*path || std::getenv("FGML_BATCH_STRIPS")) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    const std::string want = device_name();
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        char *tab = std::strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        int a, b, c;
+        if (want == line && std::sscanf(tab + 1, "%d,%d,%d", &a, &b, &c) == 3 && a > 0 && b > 0 && c >= b)
+            g_strips = {a, b, c};
+    }
+    std::fclose(f);
+}
+
+void write_tune_cache(const BatchStrips &v) {
+    const char *path = std::getenv("FGML_TUNE_CACHE");
+    if (!path || !*path) return;
+    const std::string me = device_name();
+    std::vector<std::string> keep;
+    if (FILE *f = std::fopen(path, "r")) {
+        char line[512];
+        while (std::fgets(line, sizeof line, f)) {
+            const char *tab = std::strchr(line, '\t');
+            if (tab && std::string(line, (size_t)(tab - line)) == me) continue;
+            keep.push_back(line);
+        }
+        std::fclose(f);
+    }
+    if (FILE *f = std::fopen(path, "w")) {
+        for (const std::string &l : keep) std::fputs(l.c_str(), f);
+        std::fprintf(f, "%s\t%d,%d,%d\n", me.c_str(), v.per_sm, v.lo, v.hi);
+        std::fclose(f);
+    }
+}
+
 int batch_strip_rows(int w, int h) {
     BatchStrips v;
     {
         std::lock_guard<std::mutex> lk(g_strips_mu);
+        if (!g_strips_cache_read) read_tune_cache();
         v = g_strips;
     }
     const int nx = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
@@ -1304,6 +1373,7 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
                                        const fg_params *params, fg_image *F, fg_image *B,
                                        void *stream) {
     g_err.clear();
+    Range range("fg_estimate_batch");
     if (n < 1 || !I || !alpha || !F || !B) return fail(FG_ERR_INVALID_ARG, "empty batch or NULL array");
     fg_status st;
     const fg_params p = params_or_default(params);
@@ -1619,8 +1689,10 @@ extern "C" fg_status fg_autotune_batch(int n, const fg_image *I, const fg_image 
     {
         std::lock_guard<std::mutex> lk(g_strips_mu);
         g_strips = st == FG_OK && best >= 0 ? kStripCandidates[best] : keep;
+        g_strips_cache_read = true;
     }
     if (st != FG_OK) return st;
+    write_tune_cache(kStripCandidates[best]);
     if (chosen) *chosen = best;
     if (ms) *ms = best_ms / 2;
     return FG_OK;

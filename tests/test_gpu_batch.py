@@ -120,3 +120,19 @@ def test_autotune_picks_a_strip_shape_and_results_do_not_change(fgml):
     fgml.sync()
     for (F0, B0), (F1, B1) in zip(before, after):
         assert torch.equal(F0, F1) and torch.equal(B0, B1)
+
+
+def test_autotune_writes_the_tune_cache(fgml, tmp_path, monkeypatch):
+    path = tmp_path / "tune.txt"
+    path.write_text("Some Other GPU\t1,2,3\n")
+    monkeypatch.setenv("FGML_TUNE_CACHE", str(path))
+    ss = _samples([(300, 211), (640, 480)], 1100)
+    imgs = [(_dev(s.I), _dev(s.alpha)) for s in ss]
+    chosen, _ = fgml.autotune_batch(imgs)
+    lines = path.read_text().splitlines()
+    assert lines[0] == "Some Other GPU\t1,2,3"          # other models' lines are kept
+    name = torch.cuda.get_device_name(0)
+    mine = [l for l in lines if l.startswith(name + "\t")]
+    assert len(mine) == 1
+    per_sm, lo, hi = (int(v) for v in mine[0].split("\t")[1].split(","))
+    assert per_sm > 0 and 0 < lo <= hi

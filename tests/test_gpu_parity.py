@@ -251,3 +251,43 @@ def test_debug_input_range_check(fgml, monkeypatch):
     monkeypatch.delenv("FGML_DEBUG")
     fgml.estimate(nan_I, A)      # unchecked: the call itself succeeds
     torch.cuda.synchronize()
+
+
+def test_allocation_failure_is_reported_and_recoverable(fgml, monkeypatch):
+    # the workspace of a fresh stream cannot grow: the call reports FG_ERR_OOM, launches
+    # nothing, and works once allocation is allowed again
+    s = synth.make_sample(700, 500, 4500)
+    I = torch.from_numpy(s.I).cuda()
+    A = torch.from_numpy(s.alpha).cuda()
+    st = torch.cuda.Stream()
+    monkeypatch.setenv("FGML_FAIL_ALLOC", "1")
+    with pytest.raises(fgml.FgmlError) as e:
+        fgml.estimate(I, A, stream=st)
+    assert e.value.status == fgml.FG_ERR_OOM
+    monkeypatch.delenv("FGML_FAIL_ALLOC")
+    F, B = fgml.estimate(I, A, stream=st)
+    st.synchronize()
+    F0, B0 = fgml.estimate(I, A)
+    torch.cuda.synchronize()
+    assert torch.equal(F, F0) and torch.equal(B, B0)
+    fgml.release_workspace(st)
+
+
+def test_outputs_leave_guard_bands_untouched(fgml):
+    # F and B inside larger buffers: rows padded with guard columns and guard rows above and
+    # below, all filled with a sentinel that the solve must not touch
+    w, h, g = 517, 389, 7
+    s = synth.make_sample(w, h, 4600)
+    I = torch.from_numpy(s.I).cuda()
+    A = torch.from_numpy(s.alpha).cuda()
+    sentinel = -12345.0
+    bufs = [torch.full((h + 2 * g, 3 * w + 2 * 3 * g), sentinel, device="cuda") for _ in range(2)]
+    F, B = (b[g:g + h, 3 * g:3 * g + 3 * w].view(h, w, 3) for b in bufs)
+    fgml.estimate(I, A, None, F, B)
+    torch.cuda.synchronize()
+    for b in bufs:
+        inner = torch.zeros_like(b, dtype=torch.bool)
+        inner[g:g + h, 3 * g:3 * g + 3 * w] = True
+        assert bool((b[~inner] == sentinel).all())
+    Fo, Bo = oracle.ml(s.I, s.alpha)
+    assert np.abs(F.cpu().numpy() - Fo).max() <= 1e-4
