@@ -173,7 +173,9 @@ def cpu_baseline(sample: str, seconds: float = 10.0):
 
 def batch_section(fgml, synth, torch, dev, timed, world, args):
     """64 images with sides log-uniform in [256, 2048]: one fg_estimate_batch call against
-    the same images solved one at a time, both on device-resident inputs."""
+    the same images solved one at a time with float32 storage (the plain form), both on
+    device-resident inputs; then the same batch with bfloat16 storage (I, alpha, F, B in
+    16 bits, every solve in float32) and its largest difference to the float32 batch."""
     ss = synth.batch(64)
     imgs = [(torch.from_numpy(s.I).to(dev), torch.from_numpy(s.alpha).to(dev)) for s in ss]
     outs = [(torch.empty_like(I), torch.empty_like(I)) for I, _ in imgs]
@@ -187,10 +189,23 @@ def batch_section(fgml, synth, torch, dev, timed, world, args):
         for (I, A), (F, B) in zip(imgs, outs):
             fgml.estimate(I, A, None, F, B)
     ms_1 = timed(one_by_one, steps, args.warmup)
+    # bfloat16 storage, same images and work list
+    imgs16 = [(I.to(torch.bfloat16), A.to(torch.bfloat16)) for I, A in imgs]
+    outs16 = [(torch.empty_like(I), torch.empty_like(I)) for I, _ in imgs16]
+    fgml.autotune_batch(imgs16, None, outs16)
+    ms_16 = timed(lambda: fgml.estimate_batch(imgs16, None, outs16), steps, args.warmup)
+    fgml.estimate_batch(imgs, None, outs)
+    torch.cuda.synchronize()
+    d16 = max(max(float((F16.float() - F).abs().max()), float((B16.float() - B).abs().max()))
+              for (F16, B16), (F, B) in zip(outs16, outs))
+    del imgs16, outs16
     return {"workload": "batch_64_uneven_256_2048_fp32", "images": len(ss), "pixels": int(npx),
             "value": world * npx / (ms_b * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms_b,
             "one_at_a_time": {"value": world * npx / (ms_1 * 1e-3) / 1e6, "unit": "Mpix/s",
                               "ms_per_step": ms_1},
+            "bf16": {"value": world * npx / (ms_16 * 1e-3) / 1e6, "unit": "Mpix/s",
+                     "ms_per_step": ms_16, "max_abs_vs_f32_batch": d16,
+                     "vs_f32_one_at_a_time": ms_1 / ms_16},
             # coarse levels, work list, and the row-aligned copy when some rows are off the
             # 16-byte grid
             "launches_per_step": 2 + int(any((3 * s.alpha.shape[1] * 4) % 16 for s in ss)),
@@ -199,83 +214,114 @@ def batch_section(fgml, synth, torch, dev, timed, world, args):
 
 
 def serving_section(fgml, synth, torch, args):
-    """Poisson arrivals of jobs (sides log-uniform in [256, 4096], random aspect, half
-    float32 and half bfloat16, host buffers) into the continuous-batching server, at
-    several multiples of the measured one-at-a-time float32 capacity."""
+    """Poisson arrivals of jobs (sides log-uniform in [256, 4096], random aspect, host
+    buffers) into the continuous-batching server, at several multiples of the measured
+    one-at-a-time float32 capacity: the mixed workload (half float32, half bfloat16
+    requests) and the same jobs with bfloat16 storage only."""
     import threading
     rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 4))
-    templates = []
+    base = []
     for i in range(16):
         w = int(np.exp(rng.uniform(np.log(256), np.log(4096))))
         h = int(np.exp(rng.uniform(np.log(256), np.log(4096))))
         s = synth.make_sample(w, h, synth.SEED_BASE + 400 + i)
-        dt = torch.float32 if i % 2 == 0 else torch.bfloat16
-        templates.append((torch.from_numpy(s.I).to(dt).pin_memory(),
-                          torch.from_numpy(s.alpha).to(dt).pin_memory(), w * h))
-    # one-at-a-time float32 capacity through the host-buffer entry point
-    f32 = [(I.float().pin_memory(), A.float().pin_memory(), n) for I, A, n in templates]
-    # every template once first, so that workspace growth and launch-graph capture are done
-    # before the steady-state capacity is timed
-    for I, A, _ in f32:
-        fgml.estimate_host(I, A)
-    t0 = time.perf_counter()
-    for I, A, _ in f32:
-        fgml.estimate_host(I, A)
-    dt1 = time.perf_counter() - t0
-    cap_req = len(f32) / dt1
-    cap_px = sum(n for _, _, n in f32) / dt1
+        base.append((s, w * h))
+
+    def pinned(x, dt):
+        return torch.from_numpy(x).to(dt).pin_memory()
+
+    def outputs(I):   # one pinned output pair per template: the bench never reads them
+        return (torch.empty(I.shape, dtype=I.dtype, pin_memory=True),
+                torch.empty(I.shape, dtype=I.dtype, pin_memory=True))
+
+    f32 = []
+    for s, n in base:
+        I, A = pinned(s.I, torch.float32), pinned(s.alpha, torch.float32)
+        f32.append((I, A, n, outputs(I)))
+    # one-at-a-time float32 capacity through the host-buffer entry point: every template
+    # once first (workspace growth, launch-graph capture), then passes over the 16
+    # templates for at least a second, pinned outputs
+    for I, A, _, (F, B) in f32:
+        fgml.estimate_host(I, A, None, F, B)
+    calls, px, t0 = 0, 0, time.perf_counter()
+    while True:
+        for I, A, n, (F, B) in f32:
+            fgml.estimate_host(I, A, None, F, B)
+            calls += 1
+            px += n
+        dt1 = time.perf_counter() - t0
+        if dt1 >= 1.0:
+            break
+    cap_req = calls / dt1
+    cap_px = px / dt1
     out = {"workload": "serving_poisson_256_4096_mixed_f32_bf16",
-           "one_at_a_time_f32": {"req_s": cap_req, "mpix_s": cap_px / 1e6}, "rates": []}
+           "one_at_a_time_f32": {"req_s": cap_req, "mpix_s": cap_px / 1e6, "calls": calls,
+                                 "seconds": dt1},
+           "rates": [], "bf16_only": []}
+    mixed = []
+    for i, (s, n) in enumerate(base):
+        dt = torch.float32 if i % 2 == 0 else torch.bfloat16
+        I, A = pinned(s.I, dt), pinned(s.alpha, dt)
+        mixed.append((I, A, n, outputs(I)))
+    bf16 = []
+    for s, n in base:
+        I, A = pinned(s.I, torch.bfloat16), pinned(s.alpha, torch.bfloat16)
+        bf16.append((I, A, n, outputs(I)))
     n_req = max(16, args.serving_requests)
-    for x in (0.25, 0.5, 0.75, 0.9, 1.0, 1.2):
-        rate = x * cap_req
-        gaps = rng.exponential(1.0 / rate, n_req)
-        picks = rng.integers(0, len(templates), n_req)
-        with fgml.Server(streams=2, max_batch=32) as srv:
-            tickets, done, subs, lat = [], [], [], []
-            lock = threading.Lock()
-            finished = threading.Event()
 
-            def collect():
-                k = 0
-                while k < n_req:
+    def sweep(templates, rates, key):
+        for x in rates:
+            rate = x * cap_req
+            gaps = rng.exponential(1.0 / rate, n_req)
+            picks = rng.integers(0, len(templates), n_req)
+            with fgml.Server(streams=2, max_batch=32) as srv:
+                tickets, done, subs, lat = [], [], [], []
+                lock = threading.Lock()
+                finished = threading.Event()
+
+                def collect():
+                    k = 0
+                    while k < n_req:
+                        with lock:
+                            have = len(tickets)
+                        if k >= have:
+                            time.sleep(0.0002)
+                            continue
+                        t = tickets[k]
+                        srv.wait(t, 120000)
+                        a, b = srv.times(t)
+                        lat.append(b - a)
+                        done.append(b)
+                        subs.append(a)
+                        srv.release(t)
+                        k += 1
+                    finished.set()
+
+                th = threading.Thread(target=collect)
+                th.start()
+                start = time.perf_counter()
+                at = 0.0
+                for g, k in zip(gaps, picks):
+                    at += g
+                    while time.perf_counter() - start < at:
+                        pass
+                    I, A, _, (F, B) = templates[k]
+                    t = srv.submit(I, A, F, B)
                     with lock:
-                        have = len(tickets)
-                    if k >= have:
-                        time.sleep(0.0002)
-                        continue
-                    t = tickets[k]
-                    srv.wait(t, 120000)
-                    a, b = srv.times(t)
-                    lat.append(b - a)
-                    done.append(b)
-                    subs.append(a)
-                    srv.release(t)
-                    k += 1
-                finished.set()
-
-            th = threading.Thread(target=collect)
-            th.start()
-            start = time.perf_counter()
-            at = 0.0
-            for g, k in zip(gaps, picks):
-                at += g
-                while time.perf_counter() - start < at:
-                    pass
-                I, A, _ = templates[k]
-                t = srv.submit(I, A)
-                with lock:
-                    tickets.append(t)
-            finished.wait()
-            th.join()
-            st = srv.stats()
-        span = max(done) - min(subs)   # from the first arrival to the last completion
-        px = st["pixels"]
-        lat_ms = np.array(lat) * 1e3
-        out["rates"].append({"x_capacity": x, "offered_req_s": rate, "requests": n_req,
-                             "mpix_s": px / span / 1e6, "p50_ms": float(np.percentile(lat_ms, 50)),
+                        tickets.append(t)
+                finished.wait()
+                th.join()
+                st = srv.stats()
+            span = max(done) - min(subs)   # from the first arrival to the last completion
+            lat_ms = np.array(lat) * 1e3
+            out[key].append({"x_capacity": x, "offered_req_s": rate, "requests": n_req,
+                             "mpix_s": st["pixels"] / span / 1e6,
+                             "p50_ms": float(np.percentile(lat_ms, 50)),
                              "p99_ms": float(np.percentile(lat_ms, 99)), "batches": st["batches"],
                              "max_inflight": st["max_inflight"]})
+
+    sweep(mixed, (0.25, 0.5, 0.75, 0.9, 1.0, 1.2), "rates")
+    sweep(bf16, (0.5, 1.0, 1.5, 2.0), "bf16_only")
     return out
 
 
@@ -418,26 +464,29 @@ def main():
         return s, w, h, I, A, F, B
 
     peak, peak_kind = _peaks()
-    lv_src = os.path.join(ROOT, "paper_2006_14970_gb300", "csrc", "level_pass.cu")
+    lv_src = os.path.join(ROOT, "paper_2006_14970_gb300", "csrc", "level_tile.cu")
 
     def top_pass_roofline(w, h, I, A, steps, warmup, profile):
+        """The top-level pass alone (fg_level_pass: the same kernel and launch shape as
+        inside fg_estimate), from a previous level of random F and B in the storage type
+        of I, rows padded to 16 bytes like the library's own intermediate levels."""
         levels = fgml.schedule(w, h)
         (pw, ph, _), (_, _, k) = levels[-2], levels[-1]
-        # the previous level's F and B, rows padded to 16 bytes like the library's own
-        pitch = (3 * pw + 3) // 4 * 4
-        Fs = torch.rand((ph, pitch), device=dev)[:, :3 * pw].view(ph, pw, 3)
-        Bs = torch.rand((ph, pitch), device=dev)[:, :3 * pw].view(ph, pw, 3)
-        Fd = torch.empty((h, w, 3), device=dev)
-        Bd = torch.empty((h, w, 3), device=dev)
+        es = I.element_size()
+        q = 16 // es
+        pitch = (3 * pw + q - 1) // q * q
+        Fs = torch.rand((ph, pitch), device=dev).to(I.dtype)[:, :3 * pw].view(ph, pw, 3)
+        Bs = torch.rand((ph, pitch), device=dev).to(I.dtype)[:, :3 * pw].view(ph, pw, 3)
+        Fd = torch.empty((h, w, 3), device=dev, dtype=I.dtype)
+        Bd = torch.empty((h, w, 3), device=dev, dtype=I.dtype)
         ms = timed(lambda: fgml.level_pass(I, A, Fs, Bs, k, w, h, None, Fd, Bd), steps, warmup)
-        s = 4
-        algo = s * (10 * w * h + 6 * pw * ph)     # read I, alpha, previous F/B; write F, B
+        algo = es * (10 * w * h + 6 * pw * ph)     # read I, alpha, previous F/B; write F, B
         achieved = algo / (ms * 1e-3) / 1e9
-        return {"bound": "hbm", "kernel": "level_pass_tile_kernel<float,2>", "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        return {"bound": "hbm", "kernel": f"level_tile_kernel<{'float' if es == 4 else 'bf16'},2>",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                 "algorithmic_bytes": algo, "ms": ms,
-                "traffic": _traffic_from_profile(lv_src, profile)}
+                "traffic": _traffic_from_profile(lv_src, profile) if profile else None}
 
     s, w, h, I, A, F, B = image_case(WORKLOAD)
     levels = fgml.schedule(w, h)
@@ -514,7 +563,11 @@ def main():
             d = max(float((F16.float() - F8).abs().max()), float((B16.float() - B8).abs().max()))
             big["storage"][name] = {"value": world * w8 * h8 / (ms16 * 1e-3) / 1e6,
                                     "unit": "Mpix/s", "ms_per_step": ms16,
-                                    "max_abs_vs_f32_path": d}
+                                    "max_abs_vs_f32_path": d,
+                                    "vs_f32": ms8 / ms16}
+            if name == "bf16":
+                big["storage"][name]["roofline"] = top_pass_roofline(
+                    w8, h8, I16, A16, max(3, args.steps // 2), args.warmup, None)
             del I16, A16, F16, B16
 
     batch = None
@@ -536,6 +589,34 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(WORKLOAD)
 
+    # the other workloads of the metric in the line's config (the 7680x4320 image in float32
+    # and bfloat16, the batch and serving forms against float32 one image at a time)
+    secondary = {}
+    if big:
+        secondary["single_7680x4320_fp32"] = {
+            "mpix_s": big["value"], "ms_per_step": big["ms_per_step"],
+            "top_pass_hbm_frac": big["roofline"]["frac"]}
+        b16 = big["storage"].get("bf16")
+        if b16:
+            secondary["single_7680x4320_bf16"] = {
+                "mpix_s": b16["value"], "ms_per_step": b16["ms_per_step"],
+                "top_pass_hbm_frac": b16["roofline"]["frac"],
+                "max_abs_vs_f32_path": b16["max_abs_vs_f32_path"], "speedup_vs_fp32": b16["vs_f32"]}
+    if batch:
+        secondary["batch_64_uneven"] = {
+            "fp32_one_at_a_time_mpix_s": batch["one_at_a_time"]["value"],
+            "fp32_batched_mpix_s": batch["value"], "bf16_batched_mpix_s": batch["bf16"]["value"],
+            "bf16_max_abs_vs_f32": batch["bf16"]["max_abs_vs_f32_batch"]}
+    if serving:
+        best = lambda rows: max((r["mpix_s"] for r in rows), default=None)
+        secondary["serving_poisson"] = {
+            "fp32_one_at_a_time_mpix_s": serving["one_at_a_time_f32"]["mpix_s"],
+            "capacity_req_s": serving["one_at_a_time_f32"]["req_s"],
+            "mixed_best_mpix_s": best(serving["rates"]),
+            "bf16_best_mpix_s": best(serving["bf16_only"]),
+            "p50_p99_ms_at_0.75x": next(([r["p50_ms"], r["p99_ms"]] for r in serving["rates"]
+                                          if r["x_capacity"] == 0.75), None)}
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -543,7 +624,8 @@ def main():
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "single_2048x1536_hair_fp32", "w": w, "h": h,
                            "levels": len(levels), "l2": "flushed before every timed step",
-                           "parallelism": "replicas" if world > 1 else "single"},
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "secondary": secondary},
                 "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "clocks": clocks, "cpu_baseline": cpu, "big": big, "batch": batch,
                 "serving": serving, "quality": quality, "converged_reference": converged,

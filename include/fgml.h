@@ -174,14 +174,19 @@ fg_status fg_level_pass(const fg_image *I, const fg_image *alpha,
  * point exists for callers that cannot let the library call cudaMalloc, such as a
  * process whose device memory is all reserved up front by its own pool or budget, or a
  * latency-critical loop that cannot absorb cudaMalloc's implicit device synchronisation.
- * Arguments, layout, results and errors are those of fg_estimate, except:
- *  - the intermediate pyramid levels live in a fixed 64 MiB array inside the library
- *    (two 32 MiB level buffers), held by every device that loads the library until the
- *    process exits; an image whose largest intermediate level needs more (FP32 beyond
- *    about 5.6 megapixels with the default schedule) is rejected with
- *    FG_ERR_INVALID_ARG and a message giving both sizes;
- *  - the first call on a device looks up the array's device address (with that device
- *    current), so make that first call before any stream capture;
+ * Arguments, layout, results and errors are those of fg_estimate (FGML_DEBUG=1 input
+ * range check included), except:
+ *  - the intermediate pyramid levels live in a fixed array of 64 MiB + 256 bytes inside
+ *    the library (two 32 MiB level buffers and the range check's counter), held by every
+ *    device that loads the library until the process exits; an image whose largest
+ *    intermediate level needs more (FP32 beyond about 5.6 megapixels with the default
+ *    schedule) is rejected with FG_ERR_INVALID_ARG and a message giving both sizes;
+ *  - inputs whose rows are off the 16-byte grid are read in place (fg_estimate first
+ *    copies them to aligned rows in its workspace), which is slower but gives the same
+ *    results;
+ *  - the first call on a device (and the first after a cudaDeviceReset) looks up the
+ *    array's device address with that device current, so make that first call before
+ *    any stream capture;
  *  - all calls share the one array: calls whose work overlaps on the GPU (different
  *    streams, or several host threads) race and corrupt each other's results; order
  *    them on one stream or serialise them. Nothing in the array needs to start at zero:

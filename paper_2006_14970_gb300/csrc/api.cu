@@ -163,6 +163,9 @@ struct Workspace {
     Buf cg;       // vectors of fg_minimiser_cg
     Buf check;    // counter of the optional input range check
     Buf align;    // copies of I and alpha with rows on the 16-byte grid (tensor maps need it)
+    // side stream and events of the L2 prefetch that runs beside the coarse levels
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     // launch sequences of fg_estimate captured as CUDA graphs, by call signature
     std::map<std::string, cudaGraphExec_t> graphs;
     std::vector<std::string> graph_order;   // oldest first, for eviction
@@ -267,9 +270,9 @@ struct Input {
 // Rows per warp of a level pass: one wave of resident warps (two 4-warp blocks per SM)
 // when the level is wide enough, so that every warp walks one tall strip and the
 // vertical halo (2 rows above and below each strip) stays a small fraction.
-int strip_rows(int w, int h) {
+int strip_rows(int w, int h, int blocks_per_sm = 2) {
     const int nx = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
-    const long long resident = (long long)sm_count() * 2 * level_pass_warps_per_block();
+    const long long resident = (long long)sm_count() * blocks_per_sm * level_pass_warps_per_block();
     const long long ny = std::max<long long>(1, resident / nx);
     long long r = (h + ny - 1) / ny;
     return (int)std::max<long long>(r, 1);
@@ -285,7 +288,7 @@ long long small_level_pixels() {
     return v;
 }
 
-// Shared memory of one ring- or tile-variant block; two blocks must fit on an SM.
+// Shared memory of one ring-variant block; two blocks must fit on an SM.
 constexpr size_t kRingSmemBudget = 110 * 1024;
 
 // ------------------------------------------------------------------ tensor maps
@@ -357,34 +360,46 @@ bool pick_unit(long long rowbytes, int span, bool padded, long long pitch, int &
     return false;
 }
 
-// Fills the tile-variant fields of `a` and builds its maps; false if not applicable.
-bool plan_tile(int dtype, const Input &in, const State &src, PassArgs &a, TileMaps &m) {
+// Chunk layout of a level_tile pass: each image is gathered through a tensor map where
+// its layout allows one and the strip's source span fits one box, and is otherwise copied
+// by the lanes (their own pixels only). False if a 16-bit image would need per-lane copies
+// but its base or row pitch is off the 4-byte grid (4-byte copies would then straddle).
+bool plan_chunks(int dtype, const Input &in, const State &src, PassArgs &a, TileMaps &m) {
     const int es = dtype == kF32 ? 4 : 2;
     auto r128 = [](int v) { return (v + 127) & ~127; };
+    const int R = level_pass_tile_rows();
     const int spanI = strip_span(in.w, a.w), spanS = strip_span(src.w, a.w);
     const long long rbI = 3LL * in.w * es, rbA = (long long)in.w * es, rbS = 3LL * src.w * es;
-    long long inI, inA, inS;
-    if (!pick_unit(rbI, 3 * spanI * es, in.padded, in.I_pitch * es, a.tile_uI, a.tile_bwI, inI) ||
-        !pick_unit(rbA, spanI * es, in.padded, in.A_pitch * es, a.tile_uA, a.tile_bwA, inA) ||
-        !pick_unit(rbS, 3 * spanS * es, src.padded, src.pitch * es, a.tile_uS, a.tile_bwS, inS))
+    long long inI = 0, inA = 0, inS = 0;
+    const bool tI = pick_unit(rbI, 3 * spanI * es, in.padded, in.I_pitch * es, a.tile_uI, a.tile_bwI, inI) &&
+                    make_map(&m.I, in.I, inI, in.h, in.I_pitch * es, a.tile_bwI, a.tile_uI);
+    const bool tA = pick_unit(rbA, spanI * es, in.padded, in.A_pitch * es, a.tile_uA, a.tile_bwA, inA) &&
+                    make_map(&m.A, in.A, inA, in.h, in.A_pitch * es, a.tile_bwA, a.tile_uA);
+    const bool tS = pick_unit(rbS, 3 * spanS * es, src.padded, src.pitch * es, a.tile_uS, a.tile_bwS, inS) &&
+                    make_map(&m.F, src.F, inS, src.h, src.pitch * es, a.tile_bwS, a.tile_uS) &&
+                    make_map(&m.B, src.B, inS, src.h, src.pitch * es, a.tile_bwS, a.tile_uS);
+    auto words_ok = [&](const void *base, long long pitch_bytes) {
+        return es == 4 || (((uintptr_t)base & 3) == 0 && (pitch_bytes & 3) == 0);
+    };
+    if ((!tI && !words_ok(in.I, in.I_pitch * es)) || (!tA && !words_ok(in.A, in.A_pitch * es)) ||
+        (!tS && !(words_ok(src.F, src.pitch * es) && words_ok(src.B, src.pitch * es))))
         return false;
-    const int R = level_pass_tile_rows();
-    const int rowI = a.tile_bwI * a.tile_uI, rowA = a.tile_bwA * a.tile_uA, rowS = a.tile_bwS * a.tile_uS;
-    a.tile_offA = r128(R * rowI);
-    a.tile_offF = a.tile_offA + r128(R * rowA);
-    a.tile_offB = a.tile_offF + r128(R * rowS);
-    a.tile_chunk = a.tile_offB + r128(R * rowS);
-    a.tile_tx = R * (rowI + rowA + 2 * rowS);
-    if (level_pass_tile_smem(a.tile_chunk, 3) <= kRingSmemBudget)
-        a.tile_slots = 3;
-    else if (level_pass_tile_smem(a.tile_chunk, 2) <= kRingSmemBudget)
-        a.tile_slots = 2;
-    else
-        return false;
-    return make_map(&m.I, in.I, inI, in.h, in.I_pitch * es, a.tile_bwI, a.tile_uI) &&
-           make_map(&m.A, in.A, inA, in.h, in.A_pitch * es, a.tile_bwA, a.tile_uA) &&
-           make_map(&m.F, src.F, inS, src.h, src.pitch * es, a.tile_bwS, a.tile_uS) &&
-           make_map(&m.B, src.B, inS, src.h, src.pitch * es, a.tile_bwS, a.tile_uS);
+    // images copied by the lanes keep valid (unused) box units for the kernel's set-up
+    if (!tI) a.tile_uI = 8;
+    if (!tA) a.tile_uA = 8;
+    if (!tS) a.tile_uS = 8;
+    a.lt_mode[0] = !tI;
+    a.lt_mode[1] = !tA;
+    a.lt_mode[2] = a.lt_mode[3] = !tS;
+    const int lane_px = es == 4 ? 24 : 16;   // bytes per lane of a 3-channel image (two pixels)
+    a.lt_row[0] = tI ? a.tile_bwI * a.tile_uI : 32 * lane_px;
+    a.lt_row[1] = tA ? a.tile_bwA * a.tile_uA : 32 * 8;
+    a.lt_row[2] = a.lt_row[3] = tS ? a.tile_bwS * a.tile_uS : 32 * lane_px;
+    a.lt_off[0] = 0;
+    for (int k = 0; k < 3; ++k) a.lt_off[k + 1] = a.lt_off[k] + r128(R * a.lt_row[k]);
+    a.tile_chunk = a.lt_off[3] + r128(R * a.lt_row[3]);
+    a.tile_tx = R * ((tI ? a.lt_row[0] : 0) + (tA ? a.lt_row[1] : 0) + (tS ? 2 * a.lt_row[2] : 0));
+    return true;
 }
 
 // Compositing epilogue of the last pass of a solve (fg_estimate_composite).
@@ -433,7 +448,30 @@ cudaError_t pass(int dtype, int iters, int clamp, const fg_params &p, const Inpu
         return launch_level_small(dtype, iters, clamp, a, s);
     if (iters == 1 || iters == 2) {
         TileMaps maps;
-        if (plan_tile(dtype, in, src, a, maps)) return launch_level_pass_tile(dtype, iters, clamp, a, maps, s);
+        if (plan_chunks(dtype, in, src, a, maps)) {
+            // the most resident warps, then the most chunks in flight
+            int best_occ = 0, best_slots = 0;
+            for (int sl : {3, 2}) {
+                a.tile_slots = sl;
+                int occ = 0;
+                if (launch_level_tile(dtype, iters, clamp, a, maps, s, &occ) != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                if (occ > best_occ) {
+                    best_occ = occ;
+                    best_slots = sl;
+                }
+            }
+            if (best_occ > 0) {
+                a.tile_slots = best_slots;
+                a.strip_h = strip_rows(w, h, best_occ);
+                a.n_warps = a.n_xstrips * ((h + a.strip_h - 1) / a.strip_h);
+                return launch_level_tile(dtype, iters, clamp, a, maps, s, nullptr);
+            }
+        }
+        // 16-bit rows off the 4-byte grid whose levels cannot be gathered through tensor
+        // maps: the row-ring or plain-load kernels
         // ring slots: each segment's 16-byte aligned superset (up to 30 extra bytes)
         const int es = dtype == kF32 ? 4 : 2;
         auto r16 = [](int v) { return (v + 15) & ~15; };
@@ -494,11 +532,22 @@ bool rows_on_grid(const void *ptr, long long pitch_bytes) {
     return ((uintptr_t)ptr & 15) == 0 && (pitch_bytes & 15) == 0;
 }
 
+// L2 prefetch of the input beside the latency-bound levels: the coarse and small levels
+// use few SMs and little bandwidth, so while they run a side stream prefetches I and alpha
+// into L2, and the first level pass of at least an eighth of the input's pixels (the
+// first that reads many input rows) waits for it. Only inputs that fit in half of L2.
+struct Prefetch {
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
+constexpr long long kPrefetchMaxBytes = 64LL << 20;
+
 // The kernels of one solve, enqueued on `s` (no allocation, no synchronisation).
 fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
                           const std::vector<Level> &lv, int nc, void *Fd, void *Bd,
                           long long d_pitch, Workspace &ws, int es, cudaStream_t s,
-                          const Composite *cmp = nullptr, const Input *staged_from = nullptr) {
+                          const Composite *cmp = nullptr, const Input *staged_from = nullptr,
+                          const Prefetch *pf = nullptr) {
     if (staged_from) {
         // I and alpha into their row-aligned copies (`in` describes the copies)
         const Input &o = *staged_from;
@@ -551,14 +600,32 @@ fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
         ca.Bd = (void *)src.B;
         ca.d_pitch = src.pitch;
     }
+    bool joined = true;
+    if (pf) {
+        const long long bI = ((long long)(in.h - 1) * in.I_pitch + 3LL * in.w) * es;
+        const long long bA = ((long long)(in.h - 1) * in.A_pitch + in.w) * es;
+        cudaError_t e = cudaEventRecord(pf->fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(pf->side, pf->fork, 0);
+        if (e == cudaSuccess) e = launch_prefetch_l2(in.I, bI, in.A, bA, pf->side);
+        if (e == cudaSuccess) e = cudaEventRecord(pf->join, pf->side);
+        if (e != cudaSuccess) return cuda_fail(e, "L2 prefetch of the input");
+        joined = false;
+    }
     cudaError_t e = launch_coarse(dtype, p.clamp, ca, s);
     if (e != cudaSuccess) return cuda_fail(e, "coarse kernel launch");
 
+    const long long npx = (long long)in.w * in.h;
     for (int l = nc; l < n; ++l) {
+        if (!joined && (long long)lv[l].w * lv[l].h * 8 >= npx) {
+            if ((e = cudaStreamWaitEvent(s, pf->join, 0)) != cudaSuccess) return cuda_fail(e, "joining the prefetch");
+            joined = true;
+        }
         fg_status st = run_level(dtype, p, in, src, buf, lv[l].k, lv[l].w, lv[l].h, l == n - 1,
                                  Fd, Bd, d_pitch, ws, es, s, l == n - 1 ? cmp : nullptr);
         if (st != FG_OK) return st;
     }
+    if (!joined && (e = cudaStreamWaitEvent(s, pf->join, 0)) != cudaSuccess)
+        return cuda_fail(e, "joining the prefetch");
     return FG_OK;
 }
 
@@ -628,8 +695,26 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
         run.padded = true;
     }
     const Input *from = stage ? &in : nullptr;
+    // the input's L2 prefetch beside the coarse levels, for inputs that fit (not staged
+    // copies: those were just written and are in L2 already)
+    Prefetch pf{};
+    const Prefetch *pfp = nullptr;
+    const long long in_bytes = ((long long)(in.h - 1) * in.I_pitch + 3LL * in.w) * es +
+                               ((long long)(in.h - 1) * in.A_pitch + in.w) * es;
+    if (!stage && n > nc && in_bytes <= kPrefetchMaxBytes) {
+        if (!ws.side) {
+            if (cudaStreamCreateWithFlags(&ws.side, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ws.fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ws.join, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FG_ERR_CUDA, "creating the prefetch stream and events");
+            }
+        }
+        pf = Prefetch{ws.side, ws.fork, ws.join};
+        pfp = &pf;
+    }
     if (!graphs_enabled())
-        return launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp, from);
+        return launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp, from, pfp);
 
     // the launch sequence depends on the pointers, pitches, sizes, dtype and parameters
     struct {
@@ -666,9 +751,9 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
         cudaStream_t cs = capture_stream();
         if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
-            return launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp, from);
+            return launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp, from, pfp);
         }
-        fg_status st = launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, cs, cmp, from);
+        fg_status st = launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, cs, cmp, from, pfp);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         if (st != FG_OK) {
@@ -693,15 +778,16 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
     return FG_OK;
 }
 
-// FGML_DEBUG=1: every solve first checks that I and alpha hold values in [0, 1] (no NaN)
-// and returns FG_ERR_RANGE otherwise. The check synchronises the stream.
-fg_status check_inputs(const Input &in, int dtype, cudaStream_t s) {
+bool debug_checks() {
     const char *v = std::getenv("FGML_DEBUG");
-    if (!(v && *v && *v != '0')) return FG_OK;
-    Workspace &ws = workspace_for(s);
-    fg_status st = ensure(ws.check, sizeof(unsigned long long), s);
-    if (st != FG_OK) return st;
-    unsigned long long *bad = static_cast<unsigned long long *>(ws.check.p), h = 0;
+    return v && *v && *v != '0';
+}
+
+// The input range check of FGML_DEBUG=1: counts the values of I and alpha outside [0, 1]
+// or NaN into the device word *bad and returns FG_ERR_RANGE if there are any. It
+// synchronises the stream.
+fg_status range_check(const Input &in, int dtype, unsigned long long *bad, cudaStream_t s) {
+    unsigned long long h = 0;
     cudaError_t e = cudaMemsetAsync(bad, 0, sizeof h, s);
     if (e == cudaSuccess) e = launch_range_check(dtype, in.I, in.I_pitch, in.w, in.h, 3, bad, s);
     if (e == cudaSuccess) e = launch_range_check(dtype, in.A, in.A_pitch, in.w, in.h, 1, bad, s);
@@ -710,6 +796,16 @@ fg_status check_inputs(const Input &in, int dtype, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_fail(e, "input range check");
     if (h) return fail(FG_ERR_RANGE, "%llu values of I and alpha are outside [0, 1] or NaN", h);
     return FG_OK;
+}
+
+// FGML_DEBUG=1: every solve first checks that I and alpha hold values in [0, 1] (no NaN)
+// and returns FG_ERR_RANGE otherwise; the counter lives in the stream's workspace.
+fg_status check_inputs(const Input &in, int dtype, cudaStream_t s) {
+    if (!debug_checks()) return FG_OK;
+    Workspace &ws = workspace_for(s);
+    fg_status st = ensure(ws.check, sizeof(unsigned long long), s);
+    if (st != FG_OK) return st;
+    return range_check(in, dtype, static_cast<unsigned long long *>(ws.check.p), s);
 }
 
 fg_params params_or_default(const fg_params *p) {
@@ -1069,6 +1165,12 @@ fg_status fg_release_workspace(void *stream) {
     }
     cudaStreamSynchronize(s);
     clear_graphs(w);
+    if (w.side) {
+        cudaStreamSynchronize(w.side);
+        cudaStreamDestroy(w.side);
+        cudaEventDestroy(w.fork);
+        cudaEventDestroy(w.join);
+    }
     cudaFree(w.lev[0].p);
     cudaFree(w.lev[1].p);
     cudaFree(w.stage.p);
@@ -1088,40 +1190,78 @@ const char *fg_version(void) { return "fgml 0.1 (sm_103a)"; }
 
 // ====================================================== no-allocation variant
 //
-// fg_estimate_noalloc runs the same kernels as fg_estimate, but its intermediate pyramid
-// levels live in a fixed array compiled into the library instead of a workspace taken
-// with cudaMalloc. It serves callers that must not allocate device memory from inside
-// this library: processes whose device memory is fully reserved up front by their own
-// pool or budget, and hot loops that cannot afford cudaMalloc's implicit device-wide
+// fg_estimate_noalloc runs the same launch sequence as fg_estimate, but its intermediate
+// pyramid levels live in a fixed array compiled into the library instead of a workspace
+// taken with cudaMalloc. It serves callers that must not allocate device memory from
+// inside this library: processes whose device memory is fully reserved up front by their
+// own pool or budget, and hot loops that cannot afford cudaMalloc's implicit device-wide
 // synchronisation. The array exists once per device that loads the library and stays
 // allocated until the process exits.
 
 namespace {
 
-// Two level buffers of 32 MiB each: room for every intermediate level of an FP32 image
-// of up to about 5.6 megapixels with the default schedule (twice that in BF16/FP16).
-constexpr size_t kNoAllocScratchBytes = 64ull << 20;
+// Two level buffers of 32 MiB each (room for every intermediate level of an FP32 image of
+// up to about 5.6 megapixels with the default schedule, twice that in BF16/FP16), then
+// 256 bytes for the counter of the FGML_DEBUG=1 input range check.
+constexpr size_t kNoAllocLevelBytes = 32ull << 20;
+constexpr size_t kNoAllocScratchBytes = 2 * kNoAllocLevelBytes + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[64] = {};
+// The device address of the array, looked up once per device and context: the host-side
+// symbol is only a stand-in. A context is identified by the driver's process-unique
+// context id, so after cudaDeviceReset (a new primary context, the module loaded again)
+// the address is looked up again rather than reused.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
 
-// Device address of the scratch array on the current device. The host-side symbol is
-// only a stand-in, so the address is looked up once per device (with that device
-// current) and cached.
+struct NoallocAddr {
+    unsigned long long ctx_id = 0;   // 0: not looked up (or no id available)
+    void *p = nullptr;
+};
+std::mutex g_noalloc_mu;
+NoallocAddr g_noalloc_addr[64];
+
+// Unique id of the calling thread's current context, or 0 if there is none or the driver
+// does not report ids (then every call looks the address up).
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
 fg_status noalloc_scratch(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(FG_ERR_UNSUPPORTED, "device index %d above 63", dev);
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    NoallocAddr &c = g_noalloc_addr[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!c.p || !id || c.ctx_id != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the scratch array");
-        g_noalloc_addr[dev] = p;
+        c.p = p;
+        c.ctx_id = current_ctx_id();   // the lookup may have made the primary context current
     }
-    *out = g_noalloc_addr[dev];
+    *out = c.p;
     return FG_OK;
 }
 
@@ -1131,6 +1271,7 @@ extern "C" fg_status fg_estimate_noalloc(const fg_image *I, const fg_image *alph
                                          const fg_params *params, fg_image *F, fg_image *B,
                                          void *stream) {
     g_err.clear();
+    Range range("fg_estimate_noalloc");
     fg_status st;
     if ((st = check_image(I, 3, "I")) != FG_OK) return st;
     if ((st = check_image(alpha, 1, "alpha")) != FG_OK) return st;
@@ -1161,75 +1302,38 @@ extern "C" fg_status fg_estimate_noalloc(const fg_image *I, const fg_image *alph
     for (int l = nc; l < n; ++l)
         if (l != n - 1 || split_sweeps(lv[l].k).size() > 1)
             need = std::max(need, state_bytes(lv[l].w, lv[l].h, es));
-    if (need > kNoAllocScratchBytes / 2)
+    if (need > kNoAllocLevelBytes)
         return fail(FG_ERR_INVALID_ARG,
                     "%dx%d needs two %zu-byte level buffers; the no-allocation scratch holds "
                     "two of %zu bytes (use fg_estimate)",
-                    in.w, in.h, need, kNoAllocScratchBytes / 2);
+                    in.w, in.h, need, kNoAllocLevelBytes);
 
     void *scratch = nullptr;
     if ((st = noalloc_scratch(&scratch)) != FG_OK) return st;
-    // Every byte a kernel reads from the scratch was written earlier in this call, so
-    // nothing needs clearing between calls.
+    cudaStream_t s = (cudaStream_t)stream;
+    if (debug_checks()) {
+        // the counter is the scratch's tail; range_check clears it before counting
+        auto *bad = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) +
+                                                           2 * kNoAllocLevelBytes);
+        if ((st = range_check(in, dtype, bad, s)) != FG_OK) return st;
+    }
+    // Every byte a kernel reads from the level buffers was written earlier in this call,
+    // so nothing needs clearing between calls. Inputs whose rows are off the 16-byte grid
+    // are read in place (no row-aligned copy, which would need more memory).
     Workspace ws;
     ws.lev[0].p = scratch;
-    ws.lev[0].bytes = kNoAllocScratchBytes / 2;
-    ws.lev[1].p = (char *)scratch + kNoAllocScratchBytes / 2;
-    ws.lev[1].bytes = kNoAllocScratchBytes / 2;
-    cudaStream_t s = (cudaStream_t)stream;
-    void *Fd = F->ptr, *Bd = B->ptr;
-    const long long d_pitch = F->row_pitch_bytes / es;
-
-    CoarseArgs ca;
-    std::memset(&ca, 0, sizeof ca);
-    ca.I = in.I;
-    ca.I_pitch = in.I_pitch;
-    ca.A = in.A;
-    ca.A_pitch = in.A_pitch;
-    ca.Iw = in.w;
-    ca.Ih = in.h;
-    ca.nlev = nc;
-    for (int l = 0; l < nc; ++l) {
-        ca.lw[l] = lv[l].w;
-        ca.lh[l] = lv[l].h;
-        ca.lk[l] = lv[l].k;
-        ca.off[l] = ca.total;
-        ca.total += lv[l].w * lv[l].h;
-    }
-    ca.eps = p.eps_r;
-    ca.omega = p.omega;
-    ca.init = p.init;
-    ca.order = p.order;
-    State src{};
-    int buf = -1;
-    if (nc == n) {
-        ca.Fd = Fd;
-        ca.Bd = Bd;
-        ca.d_pitch = d_pitch;
-    } else {
-        src = state_in(ws.lev[0], lv[nc - 1].w, lv[nc - 1].h, es);
-        buf = 0;
-        ca.Fd = (void *)src.F;
-        ca.Bd = (void *)src.B;
-        ca.d_pitch = src.pitch;
-    }
-    cudaError_t e = launch_coarse(dtype, p.clamp, ca, s);
-    if (e != cudaSuccess) return cuda_fail(e, "coarse kernel launch");
-    for (int l = nc; l < n; ++l) {
-        st = run_level(dtype, p, in, src, buf, lv[l].k, lv[l].w, lv[l].h, l == n - 1, Fd, Bd,
-                       d_pitch, ws, es, s);
-        if (st != FG_OK) return st;
-    }
-    return FG_OK;
+    ws.lev[0].bytes = kNoAllocLevelBytes;
+    ws.lev[1].p = static_cast<char *>(scratch) + kNoAllocLevelBytes;
+    ws.lev[1].bytes = kNoAllocLevelBytes;
+    return launch_sequence(in, dtype, p, lv, nc, F->ptr, B->ptr, F->row_pitch_bytes / es, ws, es,
+                           s);
 }
 
 // ====================================================== work-list batches
 
 namespace {
 
-constexpr int kBatchRingSlotCap = 4096;        // largest ring slot a batch pass may use
-constexpr int kBatchRegionCap = 27 * 1024;     // per-warp shared memory of the batch kernel (128 multiple)
-static_assert(kRingSlots * kBatchRingSlotCap <= kBatchRegionCap, "ring slots exceed the region");
+constexpr int kBatchRegionCap = 48 * 1024;     // per-warp shared memory of the batch kernel at most
 constexpr long long kBatchWaitNs = 2000000000; // bound of one dependency wait (2 s)
 
 // Rows per strip of a batch pass: a few waves of the persistent grid per level.
@@ -1239,8 +1343,8 @@ constexpr long long kBatchWaitNs = 2000000000; // bound of one dependency wait (
 struct BatchStrips {
     int per_sm, lo, hi;
 };
-constexpr BatchStrips kStripCandidates[] = {{4, 8, 64}, {2, 16, 128}, {8, 8, 64}, {4, 16, 96},
-                                            {2, 8, 48}, {6, 8, 64}};
+constexpr BatchStrips kStripCandidates[] = {{4, 28, 124}, {2, 60, 252}, {8, 28, 124}, {3, 44, 188},
+                                            {6, 28, 92}, {2, 28, 124}};
 std::mutex g_strips_mu;
 BatchStrips g_strips = [] {
     BatchStrips v = kStripCandidates[0];
@@ -1310,11 +1414,12 @@ int batch_strip_rows(int w, int h) {
     const int nx = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
     const long long target = (long long)sm_count() * v.per_sm;
     long long r = ((long long)h * nx + target - 1) / target;
-    return (int)std::min<long long>(std::max<long long>(r, v.lo), v.hi);
+    r = std::min<long long>(std::max<long long>(r, v.lo), v.hi);
+    return (int)((r + 3) / 4 * 4);   // whole four-row chunks with the two halo rows each side
 }
 
-PassArgs batch_pass_args(int dtype, const fg_params &p, const Input &in, const State &src,
-                         void *Fd, void *Bd, long long d_pitch, int w, int h, bool *ring) {
+PassArgs batch_pass_args(const fg_params &p, const Input &in, const State &src, void *Fd,
+                         void *Bd, long long d_pitch, int w, int h) {
     PassArgs a;
     std::memset(&a, 0, sizeof a);
     a.I = in.I;
@@ -1338,31 +1443,18 @@ PassArgs batch_pass_args(int dtype, const fg_params &p, const Input &in, const S
     a.strip_h = batch_strip_rows(w, h);
     a.n_xstrips = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
     a.n_warps = a.n_xstrips * ((h + a.strip_h - 1) / a.strip_h);
-    const int es = dtype == kF32 ? 4 : 2;
-    auto r16 = [](int v) { return (v + 15) & ~15; };
-    const int spanI = strip_span(in.w, w), spanS = strip_span(src.w, w);
-    a.capI = r16(3 * spanI * es + 30);
-    a.capA = r16(spanI * es + 30);
-    a.capS = r16(3 * spanS * es + 30);
-    a.slot_bytes = a.capI + a.capA + 2 * a.capS;
-    a.I_end = (const char *)in.I + ((long long)(in.h - 1) * in.I_pitch + 3LL * in.w) * es;
-    a.A_end = (const char *)in.A + ((long long)(in.h - 1) * in.A_pitch + in.w) * es;
-    a.Fs_end = (const char *)src.F + ((long long)(src.h - 1) * src.pitch + 3LL * src.w) * es;
-    a.Bs_end = (const char *)src.B + ((long long)(src.h - 1) * src.pitch + 3LL * src.w) * es;
-    *ring = a.slot_bytes <= kBatchRingSlotCap;
-    if (!*ring) a.capI = a.capA = a.capS = a.slot_bytes = 0;
     return a;
 }
 
 fg_status batch_launch(int dtype, int clamp, BatchLaunch &b, cudaStream_t s) {
     int per_sm = 0;
-    cudaError_t e = launch_level_batch(dtype, clamp, b, s, &per_sm);
+    cudaError_t e = launch_tile_batch(dtype, clamp, b, s, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel occupancy");
     if (per_sm < 1) return fail(FG_ERR_CUDA, "batch kernel does not fit on an SM");
     b.blocks = std::max(1, std::min(per_sm * sm_count(),
                                      (b.n_items + level_pass_warps_per_block() - 1) /
                                          level_pass_warps_per_block()));
-    e = launch_level_batch(dtype, clamp, b, s, nullptr);
+    e = launch_tile_batch(dtype, clamp, b, s, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
     return FG_OK;
 }
@@ -1406,6 +1498,7 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
 
     struct Img {
         Input in;
+        Input orig;            // the caller's input (in: its row-aligned copy when staged)
         std::vector<Level> lv;
         int nc;
         size_t need;
@@ -1422,6 +1515,7 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
         Img &m = im[i];
         m.in = Input{I[i].ptr, alpha[i].ptr, I[i].row_pitch_bytes / es, alpha[i].row_pitch_bytes / es,
                      I[i].w, I[i].h};
+        m.orig = m.in;
         m.lv = plan_levels(m.in.w, m.in.h, p);
         m.nc = coarse_levels(m.lv);
         const int nl = (int)m.lv.size();
@@ -1487,7 +1581,8 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
     if ((st = ensure(ws.batch, off_bufs + buf_total + 256, s)) != FG_OK) return st;
     char *dev = (char *)ws.batch.p;
 
-    int slot_max = 16, tile_max = 0;
+    int chunk_max = 0;
+    bool planned = true;   // every pass has a chunk layout (else image by image)
     std::vector<StageJob> jobs;
     long long stage_rows = 0;
     for (int i = 0; i < n; ++i) {
@@ -1567,21 +1662,14 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
                 }
                 BatchDesc d;
                 std::memset(&d, 0, sizeof d);
-                bool ring = false;
-                d.a = batch_pass_args(dtype, p, m.in, src, Fd, Bd, dp, w, h, &ring);
+                d.a = batch_pass_args(p, m.in, src, Fd, Bd, dp, w, h);
                 d.iters = passes[j];
                 d.dep = prev;
                 d.dep_count = prev >= 0 ? descs[prev].a.n_warps : 0;
-                // rows by TMA gather where the pass's tensor maps exist and its chunks fit
-                // the per-warp region; else the ring, else plain loads
-                if (d.iters > 0 && plan_tile(dtype, m.in, src, d.a, d.maps) &&
-                    (long long)kBatchTileSlots * d.a.tile_chunk <= kBatchRegionCap) {
-                    d.tile = 1;
-                    tile_max = std::max(tile_max, kBatchTileSlots * d.a.tile_chunk);
-                    ring = false;
-                }
-                d.ring = ring ? 1 : 0;
-                if (ring) slot_max = std::max(slot_max, d.a.slot_bytes);
+                if (plan_chunks(dtype, m.in, src, d.a, d.maps))
+                    chunk_max = std::max(chunk_max, d.a.tile_chunk);
+                else
+                    planned = false;
                 prev = (int)descs.size();
                 per_image[i].push_back(prev);
                 descs.push_back(d);
@@ -1592,7 +1680,18 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
             }
         }
     }
-    // every ring pass uses the batch's largest slot layout
+    if (!planned) {
+        // a 16-bit pass whose rows would need per-lane copies off the 4-byte grid
+        for (int i = 0; i < n; ++i)
+            if ((st = estimate(im[i].orig, dtype, p, F[i].ptr, B[i].ptr, F[i].row_pitch_bytes / es, s)) != FG_OK)
+                return st;
+        return FG_OK;
+    }
+    // every warp's region holds two chunks of the largest pass; smaller passes keep as
+    // many chunks in flight as fit (at most three)
+    const int region = (2 * chunk_max + 127) & ~127;
+    if (region > kBatchRegionCap) return fail(FG_ERR_CUDA, "batch region %d exceeds the cap", region);
+    for (BatchDesc &d : descs) d.a.tile_slots = std::min(kBatchMaxSlots, region / std::max(1, d.a.tile_chunk));
     std::vector<BatchItem> items;
     items.reserve((size_t)nitems);
     for (size_t rank = 0;; ++rank) {
@@ -1605,10 +1704,6 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
         }
         if (!any) break;
     }
-    for (BatchDesc &d : descs)
-        if (d.ring) {
-            d.a.slot_bytes = slot_max;
-        }
 
     std::vector<char> blob(off_bufs, 0);
     if (!jobs.empty()) std::memcpy(blob.data() + off_jobs, jobs.data(), jobs.size() * sizeof(StageJob));
@@ -1634,10 +1729,8 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
     b.n_items = (int)items.size();
     b.counters = reinterpret_cast<int *>(dev + off_cnt);
     b.wait_ns = kBatchWaitNs;
-    b.slot_bytes = slot_max;
-    // 128-byte aligned, as the tensor copies into a warp's region require
-    b.region = (std::max(kRingSlots * slot_max, tile_max) + 127) & ~127;
-    if (b.region > kBatchRegionCap) return fail(FG_ERR_CUDA, "batch region %d exceeds the cap", b.region);
+    b.slot_bytes = 0;
+    b.region = region;   // 128-byte aligned, as the tensor copies into a warp's region require
     return batch_launch(dtype, p.clamp, b, s);
 }
 
@@ -1724,10 +1817,10 @@ extern "C" fg_status fg_selftest_bounded_wait(void *stream) {
     b.n_items = 1;
     b.counters = reinterpret_cast<int *>(dev + off_cnt);
     b.wait_ns = 20000000;   // 20 ms
-    b.slot_bytes = 16;
-    b.region = (kRingSlots * 16 + 127) & ~127;
+    b.slot_bytes = 0;
+    b.region = 128;
     b.blocks = 1;
-    e = launch_level_batch(kF32, 1, b, s, nullptr);
+    e = launch_tile_batch(kF32, 1, b, s, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "self-test synchronize");

@@ -353,8 +353,7 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs &p) {
 template <typename T, bool CLAMP>
 cudaError_t launch_t(const CoarseArgs &a, cudaStream_t s) {
     const size_t smem = coarse_smem_bytes(a.total);
-    cudaError_t e = cudaFuncSetAttribute(coarse_kernel<T, CLAMP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(coarse_kernel<T, CLAMP>);
     if (e != cudaSuccess) return e;
     return launch_pdl(coarse_kernel<T, CLAMP>, dim3(1), dim3(kThreads), smem, s, a);
 }
@@ -362,8 +361,7 @@ cudaError_t launch_t(const CoarseArgs &a, cudaStream_t s) {
 template <typename T, bool CLAMP>
 cudaError_t launch_batch_t(const CoarseArgs *list, int n, int max_total, cudaStream_t s) {
     const size_t smem = coarse_smem_bytes(max_total);
-    cudaError_t e = cudaFuncSetAttribute(coarse_batch_kernel<T, CLAMP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(coarse_batch_kernel<T, CLAMP>);
     if (e != cudaSuccess) return e;
     coarse_batch_kernel<T, CLAMP><<<n, kThreads, smem, s>>>(list);
     return cudaGetLastError();

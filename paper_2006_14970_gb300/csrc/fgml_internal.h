@@ -59,11 +59,17 @@ struct PassArgs {
     int capI, capA, capS, slot_bytes;
     // row-ring variant only: one past the last byte of I, alpha, Fs and Bs
     const void *I_end, *A_end, *Fs_end, *Bs_end;
-    // tile variant only: box widths (in elements of tile_u* bytes: 8, 4 or 2, the largest
-    // unit that divides a row), chunk layout (bytes), chunks in flight
+    // level_tile.cu: tensor-gather box widths (in elements of tile_u* bytes: 8, 4 or 2, the
+    // largest unit that divides a row) of I, alpha and the starting F and B; chunk slots in
+    // flight per warp, bytes of one chunk slot, bytes the gathers of one chunk deliver
     int tile_bwI, tile_bwA, tile_bwS, tile_slots;
     int tile_uI, tile_uA, tile_uS;
-    int tile_offA, tile_offF, tile_offB, tile_chunk, tile_tx;
+    int tile_chunk, tile_tx;
+    // chunk pipeline of level_tile.cu, per image (0 I, 1 alpha, 2 F, 3 B): rows of the
+    // image arrive by tensor gather (mode 0, box of tile_bw*/tile_u*) or by per-lane
+    // asynchronous copies of the lane's own pixels (mode 1); lt_row = bytes of one row of
+    // the image in a chunk slot, lt_off = offset of its rows in the slot
+    int lt_mode[4], lt_row[4], lt_off[4];
     // optional compositing epilogue (In == nullptr: none): as the pass stores F it also
     // writes In = alpha F + (1 - alpha) Bn at the same pixel, alpha being the level's
     const void *Bn;         // new background, w x h x 3
@@ -92,8 +98,6 @@ struct BatchDesc {
     int iters;       // sweeps of this pass (1 or 2)
     int dep;         // pass whose strips must all be done first (-1: none)
     int dep_count;   // strips of that pass
-    int ring;        // 1: rows through the TMA ring (a.cap*/slot_bytes set)
-    int tile;        // 1: rows by TMA gather from `maps` (a.tile_* set); else ring or plain loads
     TileMaps maps;   // the pass's tensor maps (64-byte aligned in the device array)
 };
 
@@ -130,18 +134,16 @@ struct StageList {
 cudaError_t launch_stage_rows(int dtype, const StageList &list, int njobs, long long total_rows,
                               cudaStream_t s);
 
+// Prefetches the byte ranges [p0, p0 + n0) and [p1, p1 + n1) into L2 (the 16-byte aligned
+// interior of each; a null pointer or n <= 0 skips a range).
+cudaError_t launch_prefetch_l2(const void *p0, long long n0, const void *p1, long long n1,
+                               cudaStream_t s);
+
 // Adds to *bad (device) the number of values of a w x h x ch image (pitch in elements)
 // outside [0, 1] or NaN (the optional input check).
 cudaError_t launch_range_check(int dtype, const void *p, long long pitch, int w, int h, int ch,
                                unsigned long long *bad, cudaStream_t s);
 
-// Tile chunks in flight per warp in the work-list kernel.
-constexpr int kBatchTileSlots = 3;
-size_t level_batch_smem(int region);
-
-// Launches the batch kernel, or (blocks_per_sm != NULL) only reports its occupancy.
-cudaError_t launch_level_batch(int dtype, int clamp, const BatchLaunch &b, cudaStream_t s,
-                               int *blocks_per_sm);
 
 // Tensor maps of the tile variant: I, alpha, and the starting F and B, as 2D tensors of
 // 8-byte elements (a row's bytes / 8), box one row high for gather-mode copies.
@@ -260,6 +262,22 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaGetLastError();
 }
 
+// Lets `kernel` use dynamic shared memory up to the device's opt-in maximum less its
+// static shared memory. The limit is always set to that largest value (never lowered), so
+// every launch and every graph node captured for the kernel, whatever its own size, stays
+// within the limit in force.
+template <typename Kern>
+cudaError_t allow_dynamic_smem(Kern *kernel) {
+    int dev = 0, most = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&most, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                most - (int)fa.sharedSizeBytes);
+}
+
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_level_pass(int dtype, int iters, int clamp, const PassArgs &a,
                               cudaStream_t s);
@@ -268,11 +286,23 @@ cudaError_t launch_level_pass(int dtype, int iters, int clamp, const PassArgs &a
 cudaError_t launch_level_pass_ring(int dtype, int iters, int clamp, const PassArgs &a,
                                    cudaStream_t s);
 size_t level_pass_ring_smem(int slot_bytes);
-// Tile variant (2D tensor copies of multi-row boxes): for levels whose I and alpha are the
-// full-resolution input; a.tile_* must be filled in and the maps built for them.
-cudaError_t launch_level_pass_tile(int dtype, int iters, int clamp, const PassArgs &a,
-                                   const TileMaps &m, cudaStream_t s);
-size_t level_pass_tile_smem(int chunk_bytes, int slots);
+
+// Level pass with reflected borders and running sums (level_tile.cu): PassArgs tile_* and
+// lt_* fields and the maps of the gathered images filled in; a.tile_slots (2 or 3) chunks
+// in flight per warp. With blocks_per_sm != NULL it only reports the occupancy.
+cudaError_t launch_level_tile(int dtype, int iters, int clamp, const PassArgs &a,
+                              const TileMaps &m, cudaStream_t s, int *blocks_per_sm);
+size_t level_tile_smem(int chunk_bytes, int slots);
+// Work-list batch over level_tile strips (level_tile.cu): a pass's slots (BatchDesc
+// a.tile_slots <= kBatchMaxSlots chunks of a.tile_chunk bytes) fill the warp's `region`
+// bytes. With blocks_per_sm != NULL it only reports the occupancy.
+constexpr int kBatchMaxSlots = 3;
+size_t tile_batch_smem(int region);
+cudaError_t launch_tile_batch(int dtype, int clamp, const BatchLaunch &b, cudaStream_t s,
+                              int *blocks_per_sm);
+// The tile pass's device error word (1 = a wait gave up), read and cleared; fg_sync reads
+// it through read_and_clear_device_error.
+cudaError_t read_and_clear_tile_error(int *code, cudaStream_t s);
 // Small-level variant: one block per 32 x 16 output tile, all sweeps in shared memory.
 // Red-black order: `iters` (1 or 2) red-black iterations of a level in one launch.
 cudaError_t launch_level_rb(int dtype, int iters, int clamp, const PassArgs &a, cudaStream_t s);

@@ -42,9 +42,6 @@ constexpr int kLaneCols = 64;        // columns held by a warp (2 per lane)
 constexpr int kWaitPolls = 1 << 20;          // try_wait polls before a wait gives up
 constexpr uint32_t kWaitHintNs = 2000;       // suspend-time hint of one poll
 constexpr int kTileRows = 4;                 // rows per tensor-copy chunk (gather mode: 4)
-#ifndef FGML_TILE_MIN_BLOCKS
-#define FGML_TILE_MIN_BLOCKS 2
-#endif
 #ifndef FGML_RING_MIN_BLOCKS
 #define FGML_RING_MIN_BLOCKS 2
 #endif
@@ -251,8 +248,8 @@ __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
-// Loads of F and B written earlier in the same launch (work-list batches) bypass the
-// per-SM caches; everything else goes through the read-only path.
+// Loads of F and B written earlier in the same launch bypass the per-SM caches;
+// everything else goes through the read-only path.
 template <typename T, bool COHERENT>
 __device__ __forceinline__ float ld_state(const T *p) {
     if (COHERENT) return to_f(__ldcg(p));
@@ -705,360 +702,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kRingMinBlocks) level_pas
     pdl_leave();
 }
 
-// Tile variant: the warp's rows arrive in chunks of kTileRows rows. A chunk is four
-// tensor copies in gather mode, each fetching the chunk's kTileRows rows of one image
-// (I, alpha, F or B) by row index: the nearest-resize source rows of the chunk's output
-// rows (Algorithm 1), so the same kernel serves the top level (I and alpha rows are the
-// input rows) and gathered levels. The tensors are viewed as rows of 8-byte elements, so
-// one box of at most 256 elements holds a strip's source span; the hardware forms the
-// addresses and fills zeros outside the images. SLOTS chunks are in flight per warp; the
-// ring bookkeeping is paid once per chunk.
-template <typename T, int SLOTS>
-struct TileSource {
-    const unsigned char *sm;   // the block's shared memory, and its shared address
-    uint32_t sbase;
-    uint32_t slots_s, bar0;
-    int lane;
-    const CUtensorMap *mI, *mA, *mF, *mB;
-    int xI, xA, xS;         // box x coordinates (8-byte elements; even)
-    int oI0, oI1, oA0, oA1, oS0, oS1;   // per-lane byte offsets of the two pixels in box rows
-    int r_first;
-    int cfill;              // chunks filled so far (counted across the strips of a warp)
-    int cbase;              // cfill when the current strip started
-    int j;                  // row of the current chunk being taken
-    int gslot;              // slot of the current chunk
-    uint32_t gpar;
-    uint32_t issued, parity;
-    RowMap fI, fS;          // source rows of the next row to fill
-
-    __device__ __forceinline__ void fill(const PassArgs &p, const Ctl &ct) {
-        const int slot = cfill % SLOTS;
-        const uint32_t par = (uint32_t)(cfill / SLOTS) & 1u;
-        // source rows of the chunk's rows (rows past the strip repeat its last row)
-        int gy[kTileRows], sy[kTileRows];
-#pragma unroll
-        for (int k = 0; k < kTileRows; ++k) {
-            const int r = r_first + (cfill - cbase) * kTileRows + k;
-            if (r <= ct.r_last) {
-                gy[k] = fI.next();
-                sy[k] = fS.next();
-            } else {
-                gy[k] = gy[k > 0 ? k - 1 : 0];
-                sy[k] = sy[k > 0 ? k - 1 : 0];
-            }
-        }
-        if (lane == 0) {
-            const uint32_t dst = slots_s + (uint32_t)slot * (uint32_t)p.tile_chunk;
-            const uint32_t bar = bar0 + 8u * (uint32_t)slot;
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         :: "r"(bar), "r"((uint32_t)p.tile_tx) : "memory");
-            gather4(dst, mI, xI, gy, bar);
-            gather4(dst + (uint32_t)p.tile_offA, mA, xA, gy, bar);
-            gather4(dst + (uint32_t)p.tile_offF, mF, xS, sy, bar);
-            gather4(dst + (uint32_t)p.tile_offB, mB, xS, sy, bar);
-        }
-        issued |= 1u << slot;
-        parity = (parity & ~(1u << slot)) | (par << slot);
-        ++cfill;
-    }
-
-    __device__ __forceinline__ static void gather4(uint32_t dst, const CUtensorMap *m, int x,
-                                                   const int *y, uint32_t bar) {
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-            :: "r"(dst), "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y[0]), "r"(y[1]),
-               "r"(y[2]), "r"(y[3]), "r"(bar)
-            : "memory");
-    }
-
-    __device__ __forceinline__ bool wait(int slot, uint32_t par) const {
-        const uint32_t bar = bar0 + 8u * (uint32_t)slot;
-        uint32_t ok = 0;
-        for (int i = 0; i < kWaitPolls && !ok; ++i) {
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-                "selp.u32 %0, 1, 0, p;\n\t}"
-                : "=r"(ok) : "r"(bar), "r"(par), "r"(kWaitHintNs) : "memory");
-        }
-        return __all_sync(kFull, ok != 0);
-    }
-
-    // Slot and phase counters (cfill, gslot, gpar) start at 0 once per warp (init) and run
-    // on across strips, so the mbarriers are initialised once; every strip takes all the
-    // chunks it fills, so nothing is in flight between strips.
-    // A strip's maps, box x coordinates (the first source byte rounded down to 16, in
-    // elements of the map's unit) and the lane's byte offsets inside the box rows.
-    __device__ __forceinline__ void setup(const PassArgs &p, const LaneGeo &g, const CUtensorMap *I_,
-                                          const CUtensorMap *A_, const CUtensorMap *F_,
-                                          const CUtensorMap *B_) {
-        mI = I_;
-        mA = A_;
-        mF = F_;
-        mB = B_;
-        const int es = (int)sizeof(T);
-        const int X0 = g.x - 2 * lane;
-        const int xf = min(max(X0, 0), p.w - 1);
-        const int giF = nearest_src(xf, p.Iw, p.w);
-        const int gsF = nearest_src(xf, p.sw, p.w);
-        xI = (3 * giF * es) / 16 * (16 / p.tile_uI);
-        xA = (giF * es) / 16 * (16 / p.tile_uA);
-        xS = (3 * gsF * es) / 16 * (16 / p.tile_uS);
-        oI0 = 3 * g.gi0 * es - p.tile_uI * xI;
-        oI1 = 3 * g.gi1 * es - p.tile_uI * xI;
-        oA0 = g.gi0 * es - p.tile_uA * xA;
-        oA1 = g.gi1 * es - p.tile_uA * xA;
-        oS0 = 3 * g.gs0 * es - p.tile_uS * xS;
-        oS1 = 3 * g.gs1 * es - p.tile_uS * xS;
-    }
-
-    __device__ __forceinline__ void init() {
-        cfill = 0;
-        gslot = 0;
-        gpar = 0;
-    }
-
-    __device__ __forceinline__ void start(const PassArgs &p, const LaneGeo &g, const Ctl &ct) {
-        r_first = ct.r_first;
-        cbase = cfill;
-        j = 0;
-        issued = parity = 0;
-        fI.init(ct.r_first, p.Ih, p.h);
-        fS.init(ct.r_first, p.sh, p.h);
-        const int nchunks = (ct.r_last - ct.r_first) / kTileRows + 1;
-        for (int c = 0; c < SLOTS && c < nchunks; ++c) fill(p, ct);
-    }
-
-    template <typename U>
-    __device__ __forceinline__ float lds(uint32_t a) const {
-        return to_f(*reinterpret_cast<const U *>(sm + (a - sbase)));
-    }
-
-    // Two consecutive elements (one 8-byte load for float, one 4-byte for 16 bits).
-    __device__ __forceinline__ float2 lds2(uint32_t a) const {
-        const unsigned char *q = sm + (a - sbase);
-        if (sizeof(T) == 4) return *reinterpret_cast<const float2 *>(q);
-        const uint32_t v = *reinterpret_cast<const uint32_t *>(q);
-        T lo, hi;
-        const unsigned short l16 = (unsigned short)(v & 0xffffu), h16 = (unsigned short)(v >> 16);
-        memcpy(&lo, &l16, sizeof lo);
-        memcpy(&hi, &h16, sizeof hi);
-        return make_float2(to_f(lo), to_f(hi));
-    }
-
-    __device__ __forceinline__ bool get(const PassArgs &p, const LaneGeo &g, const Ctl &ct, int r,
-                                        Raw &o) {
-        if (j == 0) {
-            if (!wait(gslot, gpar)) return false;
-            issued &= ~(1u << gslot);
-        }
-        const int es = (int)sizeof(T);
-        const uint32_t base = slots_s + (uint32_t)gslot * (uint32_t)p.tile_chunk;
-        const uint32_t I = base + (uint32_t)(j * p.tile_bwI * p.tile_uI);
-        const uint32_t A = base + (uint32_t)p.tile_offA + (uint32_t)(j * p.tile_bwA * p.tile_uA);
-        const uint32_t F = base + (uint32_t)p.tile_offF + (uint32_t)(j * p.tile_bwS * p.tile_uS);
-        const uint32_t B = base + (uint32_t)p.tile_offB + (uint32_t)(j * p.tile_bwS * p.tile_uS);
-        o.a0 = lds<T>(A + oA0);
-        o.a1 = lds<T>(A + oA1);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            o.i0[c] = lds<T>(I + oI0 + c * es);
-            o.i1[c] = lds<T>(I + oI1 + c * es);
-            o.f0[c] = lds<T>(F + oS0 + c * es);
-            o.f1[c] = lds<T>(F + oS1 + c * es);
-            o.b0[c] = lds<T>(B + oS0 + c * es);
-            o.b1[c] = lds<T>(B + oS1 + c * es);
-        }
-        if (++j == kTileRows || r == ct.r_last) {
-            // the chunk is used up: refill its slot with the chunk SLOTS ahead
-            __syncwarp();
-            j = 0;
-            if (r_first + (cfill - cbase) * kTileRows <= ct.r_last) fill(p, ct);
-            if (++gslot == SLOTS) {
-                gslot = 0;
-                gpar ^= 1u;
-            }
-        }
-        return true;
-    }
-
-    __device__ __forceinline__ void abort() const {
-        for (int s = 0; s < SLOTS; ++s)
-            if (issued & (1u << s)) wait(s, (parity >> s) & 1u);
-    }
-};
-
-template <typename T, int K, bool CLAMP, int SLOTS>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, FGML_TILE_MIN_BLOCKS) level_pass_tile_kernel(
-    const PassArgs p, const __grid_constant__ CUtensorMap mI, const __grid_constant__ CUtensorMap mA,
-    const __grid_constant__ CUtensorMap mF, const __grid_constant__ CUtensorMap mB) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    pdl_enter();
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (warp >= p.n_warps) return;
-    LaneGeo g;
-    Ctl ct;
-    Out out;
-    lane_setup<T>(p, warp, lane, g, ct, out, K);
-
-    TileSource<T, SLOTS> src;
-    src.sm = smem;
-    src.sbase = smem_addr(smem);
-    src.lane = lane;
-    src.slots_s = smem_addr(smem) + (uint32_t)(wib * SLOTS * p.tile_chunk);
-    src.bar0 = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * SLOTS * p.tile_chunk) +
-               8u * (uint32_t)(wib * SLOTS);
-    src.init();
-    src.setup(p, g, &mI, &mA, &mF, &mB);
-    if (lane == 0) {
-        for (int s = 0; s < SLOTS; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(src.bar0 + 8u * s) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    run_strip<T, K, CLAMP>(p, g, ct, out, src);
-    pdl_leave();
-}
-
-// Work-list batch: one persistent launch runs the level passes of many images. Each
-// warp pops (level pass, strip) items in list order; an item first waits (bounded, with
-// backoff) until every strip of the pass it depends on has finished, then runs like a
-// strip of the ring or register variant, then counts itself done. The list holds every
-// pass after the passes it depends on, and the grid is no larger than what is resident,
-// so the items an item waits for are always running or finished. The ring's slot and
-// phase counters carry over from item to item, so its mbarriers are initialised once.
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool wait_count(const int *c, int need, long long budget_ns) {
-    const unsigned long long t0 = global_ns();
-    unsigned ns = 32;
-    for (int i = 0; i < (1 << 26); ++i) {
-        int v;
-        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
-        if (v >= need) return true;
-        if ((long long)(global_ns() - t0) > budget_ns) return false;
-        __nanosleep(ns);
-        if (ns < 1024) ns *= 2;
-    }
-    return false;
-}
-
-template <typename T, bool CLAMP>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) level_batch_kernel(
-    const BatchDesc *descs, const BatchItem *items, int n_items, int *counters,
-    long long wait_ns, int slot_bytes, int region) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ PassArgs sp[kWarpsPerBlock];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    // per warp: one `region` of bytes shared by the ring slots and the tile chunks (a
-    // strip takes everything it loads, so the two never hold data at the same time), then
-    // the ring's and the tile's mbarriers
-    const uint32_t base = smem_addr(smem) + (uint32_t)(wib * region);
-    const uint32_t bars = smem_addr(smem) + (uint32_t)(kWarpsPerBlock * region);
-
-    RingSource<T> ring;
-    ring.sm = smem;
-    ring.sbase = smem_addr(smem);
-    ring.lane = lane;
-    ring.slots_s = base;
-    ring.bar0 = bars + 8u * (uint32_t)(wib * kRingSlots);
-    ring.fslot = ring.gslot = 0;
-    ring.fpar = ring.gpar = 0;
-    ring.issued = ring.parity = 0;
-    TileSource<T, kBatchTileSlots> tile;
-    tile.sm = smem;
-    tile.sbase = smem_addr(smem);
-    tile.lane = lane;
-    tile.slots_s = base;
-    tile.bar0 = bars + 8u * (uint32_t)(kWarpsPerBlock * kRingSlots + wib * kBatchTileSlots);
-    tile.init();
-    if (lane == 0) {
-        for (int s = 0; s < kRingSlots; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(ring.bar0 + 8u * s) : "memory");
-        for (int s = 0; s < kBatchTileSlots; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tile.bar0 + 8u * s) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-
-    for (;;) {
-        int idx = 0;
-        if (lane == 0) idx = atomicAdd(&counters[0], 1);
-        idx = __shfl_sync(kFull, idx, 0);
-        if (idx >= n_items) break;
-        const BatchItem it = items[idx];
-        const BatchDesc &d = descs[it.desc];
-        const int *src_words = reinterpret_cast<const int *>(&d.a);
-        int *dst_words = reinterpret_cast<int *>(&sp[wib]);
-        for (int k = lane; k < (int)(sizeof(PassArgs) / sizeof(int)); k += 32) dst_words[k] = src_words[k];
-        const int iters = d.iters, dep = d.dep, dep_count = d.dep_count, use_ring = d.ring,
-                  use_tile = d.tile;
-        __syncwarp();
-        const PassArgs &p = sp[wib];
-        if (dep >= 0) {
-            int ok = 1;
-            if (lane == 0) ok = wait_count(&counters[1 + dep], dep_count, wait_ns) ? 1 : 0;
-            ok = __shfl_sync(kFull, ok, 0);
-            if (!ok) {
-                if (lane == 0) atomicExch(&g_device_error, 2);
-                break;
-            }
-            __threadfence();
-            asm volatile("fence.proxy.async.global;" ::: "memory");
-        }
-        LaneGeo g;
-        Ctl ct;
-        Out out;
-        bool ok;
-        if (use_tile) {
-            const TileMaps &m = d.maps;
-            if (iters == 1) {
-                lane_setup<T>(p, it.warp, lane, g, ct, out, 1);
-                tile.setup(p, g, &m.I, &m.A, &m.F, &m.B);
-                ok = run_strip<T, 1, CLAMP>(p, g, ct, out, tile);
-            } else {
-                lane_setup<T>(p, it.warp, lane, g, ct, out, 2);
-                tile.setup(p, g, &m.I, &m.A, &m.F, &m.B);
-                ok = run_strip<T, 2, CLAMP>(p, g, ct, out, tile);
-            }
-        } else if (use_ring) {
-            if (iters == 1) {
-                lane_setup<T>(p, it.warp, lane, g, ct, out, 1);
-                ring.setup(p, g, lane);
-                ok = run_strip<T, 1, CLAMP>(p, g, ct, out, ring);
-            } else {
-                lane_setup<T>(p, it.warp, lane, g, ct, out, 2);
-                ring.setup(p, g, lane);
-                ok = run_strip<T, 2, CLAMP>(p, g, ct, out, ring);
-            }
-        } else {
-            RegSource<T, true> reg;
-            if (iters == 1) {
-                lane_setup<T>(p, it.warp, lane, g, ct, out, 1);
-                ok = run_strip<T, 1, CLAMP>(p, g, ct, out, reg);
-            } else {
-                lane_setup<T>(p, it.warp, lane, g, ct, out, 2);
-                ok = run_strip<T, 2, CLAMP>(p, g, ct, out, reg);
-            }
-        }
-        if (!ok) break;
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence();
-            atomicAdd(&counters[1 + it.desc], 1);
-        }
-    }
-}
-
 // Zero sweeps: the level's F and B are the nearest resize of the starting state.
 template <typename T>
 __global__ void resize_fb_kernel(const PassArgs p) {
@@ -1096,34 +739,9 @@ template <typename T, int K, bool CLAMP>
 cudaError_t launch_ring_t(const PassArgs &a, cudaStream_t s) {
     const int blocks = (a.n_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const size_t smem = level_pass_ring_smem(a.slot_bytes);
-    cudaError_t e = cudaFuncSetAttribute(level_pass_ring_kernel<T, K, CLAMP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(level_pass_ring_kernel<T, K, CLAMP>);
     if (e != cudaSuccess) return e;
     return launch_pdl(level_pass_ring_kernel<T, K, CLAMP>, dim3(blocks), dim3(kWarpsPerBlock * 32), smem, s, a);
-}
-
-template <typename T, int K, bool CLAMP, int SLOTS>
-cudaError_t launch_tile_t(const PassArgs &a, const TileMaps &m, cudaStream_t s) {
-    const int blocks = (a.n_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const size_t smem = level_pass_tile_smem(a.tile_chunk, SLOTS);
-    cudaError_t e = cudaFuncSetAttribute(level_pass_tile_kernel<T, K, CLAMP, SLOTS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return launch_pdl(level_pass_tile_kernel<T, K, CLAMP, SLOTS>, dim3(blocks), dim3(kWarpsPerBlock * 32),
-                      smem, s, a, m.I, m.A, m.F, m.B);
-}
-
-template <typename T, int K, bool CLAMP>
-cudaError_t launch_tile_slots(const PassArgs &a, const TileMaps &m, cudaStream_t s) {
-    return a.tile_slots == 3 ? launch_tile_t<T, K, CLAMP, 3>(a, m, s) : launch_tile_t<T, K, CLAMP, 2>(a, m, s);
-}
-
-template <typename T>
-cudaError_t launch_tile_dtype(int iters, int clamp, const PassArgs &a, const TileMaps &m,
-                              cudaStream_t s) {
-    if (iters == 1) return clamp ? launch_tile_slots<T, 1, true>(a, m, s) : launch_tile_slots<T, 1, false>(a, m, s);
-    if (iters == 2) return clamp ? launch_tile_slots<T, 2, true>(a, m, s) : launch_tile_slots<T, 2, false>(a, m, s);
-    return cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -1170,52 +788,7 @@ cudaError_t launch_level_pass_ring(int dtype, int iters, int clamp, const PassAr
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_level_pass_tile(int dtype, int iters, int clamp, const PassArgs &a,
-                                   const TileMaps &m, cudaStream_t s) {
-    switch (dtype) {
-        case kF32: return launch_tile_dtype<float>(iters, clamp, a, m, s);
-        case kBF16: return launch_tile_dtype<__nv_bfloat16>(iters, clamp, a, m, s);
-        case kF16: return launch_tile_dtype<__half>(iters, clamp, a, m, s);
-    }
-    return cudaErrorInvalidValue;
-}
-
-size_t level_pass_tile_smem(int chunk_bytes, int slots) {
-    return (size_t)kWarpsPerBlock * slots * (size_t)chunk_bytes + (size_t)kWarpsPerBlock * slots * 8;
-}
-
 int level_pass_tile_rows() { return kTileRows; }
-
-template <typename T, bool CLAMP>
-cudaError_t batch_t(const BatchLaunch &b, cudaStream_t s, int *blocks_per_sm) {
-    const size_t smem = level_batch_smem(b.region);
-    cudaError_t e = cudaFuncSetAttribute(level_batch_kernel<T, CLAMP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (blocks_per_sm) {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, level_batch_kernel<T, CLAMP>,
-                                                             kWarpsPerBlock * 32, smem);
-    }
-    level_batch_kernel<T, CLAMP><<<b.blocks, kWarpsPerBlock * 32, smem, s>>>(
-        b.descs, b.items, b.n_items, b.counters, b.wait_ns, b.slot_bytes, b.region);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_level_batch(int dtype, int clamp, const BatchLaunch &b, cudaStream_t s,
-                               int *blocks_per_sm) {
-    switch (dtype) {
-        case kF32: return clamp ? batch_t<float, true>(b, s, blocks_per_sm) : batch_t<float, false>(b, s, blocks_per_sm);
-        case kBF16:
-            return clamp ? batch_t<__nv_bfloat16, true>(b, s, blocks_per_sm)
-                         : batch_t<__nv_bfloat16, false>(b, s, blocks_per_sm);
-        case kF16: return clamp ? batch_t<__half, true>(b, s, blocks_per_sm) : batch_t<__half, false>(b, s, blocks_per_sm);
-    }
-    return cudaErrorInvalidValue;
-}
-
-size_t level_batch_smem(int region) {
-    return (size_t)kWarpsPerBlock * (size_t)region + (size_t)kWarpsPerBlock * (kRingSlots + kBatchTileSlots) * 8;
-}
 
 size_t level_pass_ring_smem(int slot_bytes) {
     return (size_t)kWarpsPerBlock * kRingSlots * (size_t)slot_bytes +
@@ -1245,7 +818,11 @@ cudaError_t read_and_clear_device_error(int *code, cudaStream_t s) {
         e = cudaMemcpyToSymbolAsync(g_device_error, &zero, sizeof(int), 0,
                                     cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
     }
+    int tile = 0;   // the tile kernel's own error word (level_tile.cu)
+    e = read_and_clear_tile_error(&tile, s);
+    if (e == cudaSuccess && !*code) *code = tile;
     return e;
 }
 

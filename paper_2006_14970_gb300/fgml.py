@@ -338,8 +338,9 @@ def version() -> str:
 def estimate_noalloc(I: torch.Tensor, alpha: torch.Tensor, p: Params | None = None,
                      F: torch.Tensor | None = None, B: torch.Tensor | None = None, stream=None):
     """fg_estimate_noalloc: as ``estimate`` but the library allocates no device memory
-    (intermediate levels use its fixed 64 MiB array; larger images are rejected). For
-    callers that cannot let the library call cudaMalloc. Calls that overlap on the GPU
+    (intermediate levels use its fixed array of two 32 MiB level buffers; larger images
+    are rejected). For callers that cannot let the library call cudaMalloc, e.g. a process
+    whose device memory is all reserved by its own pool. Calls that overlap on the GPU
     share that array and race; keep them on one stream."""
     lib = load()
     fn = lib.fg_estimate_noalloc

@@ -311,6 +311,28 @@ def test_transpose_equivariance(order):
     assert np.max(np.abs(Bt.transpose(1, 0, 2) - B)) < 1e-12
 
 
+def test_red_black_sweep_updates_even_colour_first():
+    # With alpha = 1 the matrix of the 2x2 solve is diagonal (U = (1, 0)) and every edge
+    # weight is eps_r, so the background update is the plain mean of the four (clamped)
+    # neighbours: B_i <- (B_left + B_right + B_up + B_down) / 4, a clamped neighbour being
+    # the pixel's own current value. One red-black sweep on a 3x3 image that starts with
+    # B = 1 at (x, y) = (1, 0) and 0 elsewhere, worked by hand:
+    #   colour x + y even first: (0,0), (2,0), (1,1) see the 1 once -> 1/4; (0,2), (2,2) -> 0;
+    #   then the odd colour: (1,0) <- (1/4 + 1/4 + 1 [itself, clamped above] + 1/4) / 4 = 7/16,
+    #   (0,1) <- (0 [itself] + 1/4 + 1/4 + 0) / 4 = 1/8, (2,1) likewise 1/8,
+    #   (1,2) <- (0 + 0 + 1/4 + 0 [itself]) / 4 = 1/16.
+    # Odd colour first would give [[1/16, 1/4, 1/16], [0, 1/16, 0], [0, 0, 0]] instead.
+    a = np.ones((3, 3))
+    I = np.zeros((3, 3, 3))
+    F0 = np.zeros((3, 3, 3))
+    B0 = np.zeros((3, 3, 3))
+    B0[0, 1, :] = 1.0
+    F, B = oracle.level_iterate(I, a, F0, B0, 1, Params(order=REDBLACK))
+    want = np.array([[1 / 4, 7 / 16, 1 / 4], [1 / 8, 1 / 4, 1 / 8], [0.0, 1 / 16, 0.0]])
+    assert np.max(np.abs(B - want[:, :, None])) < 1e-12
+    assert np.all(F == 0.0)   # I = 0 and F = 0: the foreground stays exactly 0
+
+
 def test_constant_image_with_constant_init_is_a_fixed_point():
     _, a = _inputs(33, 45, 8)
     I = np.full((33, 45, 3), 0.625)
