@@ -241,7 +241,8 @@ fg_status fg_selftest_bounded_wait(void *stream);
 /* ------------------------------------------------------------------ serving
  * A server runs jobs submitted at any time with continuous batching on the current
  * device: a scheduler thread admits queued jobs in arrival order while a slot is free and
- * the job's device bytes fit in the HBM budget, copies their inputs up, merges every
+ * the job's device bytes fit in the HBM budget and the device's free memory at that
+ * moment, copies host inputs up (device inputs are read in place), merges every
  * admitted job not yet launched (of one dtype) into one fg_estimate_batch launch on an
  * idle compute stream, and completes jobs as their batch finishes (outputs copied back
  * to the job's host buffers). Jobs arriving while batches run join the next batch as
@@ -252,19 +253,28 @@ typedef struct fg_server fg_server;
 
 typedef struct {
     int max_inflight_jobs;       /* admitted and unfinished jobs at most (default 256) */
-    long long hbm_budget_bytes;  /* device bytes jobs may hold (<= 0: half the free memory) */
+    long long hbm_budget_bytes;  /* device bytes jobs may hold (<= 0: half the free memory at
+                                    creation); admission also keeps what jobs hold below the
+                                    device's free memory read at that moment, less a reserve */
     int streams;                 /* batches in flight at most, 1..16 (default 2) */
     int max_batch;               /* jobs per batch at most (default 64) */
     fg_params params;            /* method parameters for every job */
 } fg_server_cfg;
 
 typedef struct {
-    const void *I;       /* HOST w x h x 3, packed, element type dtype */
-    const void *alpha;   /* HOST w x h, packed */
+    const void *I;       /* w x h x 3, packed, element type dtype (host, or device: see flags) */
+    const void *alpha;   /* w x h, packed */
     int w, h;
     fg_dtype dtype;
-    void *F, *B;         /* HOST w x h x 3 outputs, written when the job is done */
+    void *F, *B;         /* w x h x 3 outputs, written when the job is done */
+    int flags;           /* FG_REQ_DEVICE_INPUT: I and alpha are device memory of the server's
+                            device (read in place, no copy up); FG_REQ_DEVICE_OUTPUT: F and B
+                            are device memory (written in place, no copy back) */
+    void *ready_event;   /* optional cudaEvent_t: device inputs are complete once it has
+                            fired (the job's launch waits for it); NULL: already complete */
 } fg_request;
+
+enum { FG_REQ_DEVICE_INPUT = 1, FG_REQ_DEVICE_OUTPUT = 2 };
 
 typedef struct {
     long long submitted, completed, failed, batches;

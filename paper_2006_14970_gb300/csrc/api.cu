@@ -169,6 +169,8 @@ struct Workspace {
     // launch sequences of fg_estimate captured as CUDA graphs, by call signature
     std::map<std::string, cudaGraphExec_t> graphs;
     std::vector<std::string> graph_order;   // oldest first, for eviction
+    // work lists owned by cached batch graphs (each graph reads its own copy)
+    std::map<std::string, Buf> graph_bufs;
 };
 
 constexpr size_t kMaxGraphs = 64;   // cached launch graphs per workspace
@@ -177,6 +179,23 @@ void clear_graphs(Workspace &ws) {
     for (auto &kv : ws.graphs) cudaGraphExecDestroy(kv.second);
     ws.graphs.clear();
     ws.graph_order.clear();
+    for (auto &kv : ws.graph_bufs) cudaFree(kv.second.p);   // waits for work still reading it
+    ws.graph_bufs.clear();
+}
+
+// Drops the oldest cached graph (and the work list it owns) once the cache is full.
+void evict_graphs(Workspace &ws) {
+    while (ws.graphs.size() >= kMaxGraphs) {
+        const std::string k = ws.graph_order.front();
+        cudaGraphExecDestroy(ws.graphs[k]);
+        ws.graphs.erase(k);
+        ws.graph_order.erase(ws.graph_order.begin());
+        auto b = ws.graph_bufs.find(k);
+        if (b != ws.graph_bufs.end()) {
+            cudaFree(b->second.p);
+            ws.graph_bufs.erase(b);
+        }
+    }
 }
 
 std::mutex g_ws_mu;
@@ -364,16 +383,28 @@ bool pick_unit(long long rowbytes, int span, bool padded, long long pitch, int &
 // its layout allows one and the strip's source span fits one box, and is otherwise copied
 // by the lanes (their own pixels only). False if a 16-bit image would need per-lane copies
 // but its base or row pitch is off the 4-byte grid (4-byte copies would then straddle).
-bool plan_chunks(int dtype, const Input &in, const State &src, PassArgs &a, TileMaps &m) {
+// With max_chunk > 0, I and alpha are copied by the lanes whenever gathering them would
+// make a chunk slot larger than max_chunk bytes (the work-list batch keeps its per-warp
+// region small enough for two blocks per SM).
+bool plan_chunks(int dtype, const Input &in, const State &src, PassArgs &a, TileMaps &m,
+                 int max_chunk = 0) {
     const int es = dtype == kF32 ? 4 : 2;
     auto r128 = [](int v) { return (v + 127) & ~127; };
     const int R = level_pass_tile_rows();
     const int spanI = strip_span(in.w, a.w), spanS = strip_span(src.w, a.w);
     const long long rbI = 3LL * in.w * es, rbA = (long long)in.w * es, rbS = 3LL * src.w * es;
     long long inI = 0, inA = 0, inS = 0;
-    const bool tI = pick_unit(rbI, 3 * spanI * es, in.padded, in.I_pitch * es, a.tile_uI, a.tile_bwI, inI) &&
+    bool fitI = true;
+    if (max_chunk > 0) {
+        // a chunk with I and alpha gathered and F and B gathered or copied (upper bound)
+        const int lane_px = es == 4 ? 24 : 16;
+        const int boxI = 3 * spanI * es + 32, boxA = spanI * es + 32;
+        const int boxS = std::max(3 * spanS * es + 32, 32 * lane_px);
+        fitI = r128(R * boxI) + r128(R * boxA) + 2 * r128(R * boxS) <= max_chunk;
+    }
+    const bool tI = fitI && pick_unit(rbI, 3 * spanI * es, in.padded, in.I_pitch * es, a.tile_uI, a.tile_bwI, inI) &&
                     make_map(&m.I, in.I, inI, in.h, in.I_pitch * es, a.tile_bwI, a.tile_uI);
-    const bool tA = pick_unit(rbA, spanI * es, in.padded, in.A_pitch * es, a.tile_uA, a.tile_bwA, inA) &&
+    const bool tA = fitI && pick_unit(rbA, spanI * es, in.padded, in.A_pitch * es, a.tile_uA, a.tile_bwA, inA) &&
                     make_map(&m.A, in.A, inA, in.h, in.A_pitch * es, a.tile_bwA, a.tile_uA);
     const bool tS = pick_unit(rbS, 3 * spanS * es, src.padded, src.pitch * es, a.tile_uS, a.tile_bwS, inS) &&
                     make_map(&m.F, src.F, inS, src.h, src.pitch * es, a.tile_bwS, a.tile_uS) &&
@@ -532,15 +563,40 @@ bool rows_on_grid(const void *ptr, long long pitch_bytes) {
     return ((uintptr_t)ptr & 15) == 0 && (pitch_bytes & 15) == 0;
 }
 
+// Whether a solve reads a row-aligned copy of its input: rows off the 16-byte grid, unless
+// FGML_STAGE=0 and the level passes can read the input in place by per-lane 4-byte copies
+// (always in float32; 16-bit rows need a base and pitch on the 4-byte grid).
+bool needs_stage(const Input &in, int es) {
+    if (rows_on_grid(in.I, in.I_pitch * es) && rows_on_grid(in.A, in.A_pitch * es)) return false;
+    static const bool allowed = [] {
+        const char *e = std::getenv("FGML_STAGE");
+        return !(e && *e == '0');
+    }();
+    if (allowed) return true;
+    auto words = [&](const void *p, long long pitch_bytes) {
+        return ((uintptr_t)p & 3) == 0 && (pitch_bytes & 3) == 0;
+    };
+    return es == 2 && !(words(in.I, in.I_pitch * es) && words(in.A, in.A_pitch * es));
+}
+
 // L2 prefetch of the input beside the latency-bound levels: the coarse and small levels
 // use few SMs and little bandwidth, so while they run a side stream prefetches I and alpha
 // into L2, and the first level pass of at least an eighth of the input's pixels (the
 // first that reads many input rows) waits for it. Only inputs that fit in half of L2.
+// FGML_PREFETCH=0 turns it off (read once per process).
 struct Prefetch {
     cudaStream_t side;
     cudaEvent_t fork, join;
 };
 constexpr long long kPrefetchMaxBytes = 64LL << 20;
+
+bool prefetch_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("FGML_PREFETCH");
+        return !(e && *e == '0');
+    }();
+    return on;
+}
 
 // The kernels of one solve, enqueued on `s` (no allocation, no synchronisation).
 fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
@@ -669,9 +725,8 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
     Workspace &ws = workspace_for(s);
     // Rows off the 16-byte grid cannot be described by tensor maps: the level passes of a
     // large image then read a row-aligned copy of I and alpha (one copy kernel, 32 bytes
-    // per pixel in FP32) instead of falling back to per-row copies.
-    const bool stage = n > nc && (long long)in.w * in.h > small_level_pixels() &&
-                       !(rows_on_grid(in.I, in.I_pitch * es) && rows_on_grid(in.A, in.A_pitch * es));
+    // per pixel in FP32), or the input in place by per-lane copies (see needs_stage).
+    const bool stage = n > nc && (long long)in.w * in.h > small_level_pixels() && needs_stage(in, es);
     const long long pI = ((3LL * in.w * es + 15) & ~15LL) / es, pA = (((long long)in.w * es + 15) & ~15LL) / es;
     const size_t offA = align256((size_t)(pI * es) * in.h);
     const size_t stage_need = stage ? offA + align256((size_t)(pA * es) * in.h) : 0;
@@ -701,7 +756,7 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
     const Prefetch *pfp = nullptr;
     const long long in_bytes = ((long long)(in.h - 1) * in.I_pitch + 3LL * in.w) * es +
                                ((long long)(in.h - 1) * in.A_pitch + in.w) * es;
-    if (!stage && n > nc && in_bytes <= kPrefetchMaxBytes) {
+    if (!stage && n > nc && in_bytes <= kPrefetchMaxBytes && prefetch_enabled()) {
         if (!ws.side) {
             if (cudaStreamCreateWithFlags(&ws.side, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&ws.fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -765,11 +820,7 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
         e = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(e, "instantiating the launch graph");
-        if (ws.graphs.size() >= kMaxGraphs) {
-            cudaGraphExecDestroy(ws.graphs[ws.graph_order.front()]);
-            ws.graphs.erase(ws.graph_order.front());
-            ws.graph_order.erase(ws.graph_order.begin());
-        }
+        evict_graphs(ws);
         it = ws.graphs.emplace(key, ex).first;
         ws.graph_order.push_back(key);
     }
@@ -949,7 +1000,8 @@ fg_status estimate_host(const void *I, const void *alpha, int w, int h, fg_dtype
         return cuda_fail(e, "copy of I to the device");
     if ((e = cudaMemcpy2DAsync(dA, pA, alpha, rowA, rowA, h, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "copy of alpha to the device");
-    Input in{dI, dA, (long long)(pI / es), (long long)(pA / es), w, h};
+    // the staging rows are padded to 16 bytes and readable up to their pitch
+    Input in{dI, dA, (long long)(pI / es), (long long)(pA / es), w, h, true};
     if ((st = estimate(in, (int)dtype, p, dF, dB, 3LL * w, s)) != FG_OK) return st;
     if ((e = cudaMemcpyAsync(F, dF, 3 * n * es, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(e, "copy of F to the host");
@@ -1334,6 +1386,7 @@ extern "C" fg_status fg_estimate_noalloc(const fg_image *I, const fg_image *alph
 namespace {
 
 constexpr int kBatchRegionCap = 48 * 1024;     // per-warp shared memory of the batch kernel at most
+constexpr int kBatchChunkCap = 13 * 1024;      // chunk slot size that keeps two blocks per SM
 constexpr long long kBatchWaitNs = 2000000000; // bound of one dependency wait (2 s)
 
 // Rows per strip of a batch pass: a few waves of the persistent grid per level.
@@ -1529,8 +1582,7 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
         m.need = align256(m.need);
         m.buf_off = buf_total;
         buf_total += 2 * m.need;
-        m.stage = m.nc < nl && !(rows_on_grid(m.in.I, m.in.I_pitch * es) &&
-                                 rows_on_grid(m.in.A, m.in.A_pitch * es));
+        m.stage = m.nc < nl && needs_stage(m.in, es);
         if (m.stage) {
             m.pI = ((3LL * m.in.w * es + 15) & ~15LL) / es;
             m.pA = (((long long)m.in.w * es + 15) & ~15LL) / es;
@@ -1548,6 +1600,42 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
             if ((st = estimate(im[i].in, dtype, p, F[i].ptr, B[i].ptr, F[i].row_pitch_bytes / es, s)) != FG_OK)
                 return st;
         return FG_OK;
+    }
+
+    // A repeated batch (same images, outputs, sizes, dtype, parameters and strip shape)
+    // replays the launch graph captured for it: no descriptors are built or uploaded again.
+    Workspace &wsb = workspace_for(s);
+    std::string key;
+    if (graphs_enabled()) {
+        BatchStrips strips;
+        {
+            std::lock_guard<std::mutex> lk(g_strips_mu);
+            if (!g_strips_cache_read) read_tune_cache();
+            strips = g_strips;
+        }
+        key.assign("batch", 5);
+        auto put = [&](const void *v, size_t k) { key.append(static_cast<const char *>(v), k); };
+        put(&n, sizeof n);
+        put(&p, sizeof p);
+        put(&strips, sizeof strips);
+        for (int i = 0; i < n; ++i) {
+            const fg_image *four[4] = {&I[i], &alpha[i], &F[i], &B[i]};
+            for (const fg_image *x : four) {   // fields only, no padding
+                put(&x->ptr, sizeof x->ptr);
+                put(&x->w, sizeof x->w);
+                put(&x->h, sizeof x->h);
+                put(&x->row_pitch_bytes, sizeof x->row_pitch_bytes);
+                put(&x->dtype, sizeof x->dtype);
+            }
+            const char stg = im[i].stage ? 1 : 0;
+            put(&stg, 1);
+        }
+        auto it = wsb.graphs.find(key);
+        if (it != wsb.graphs.end()) {
+            cudaError_t e = cudaGraphLaunch(it->second, s);
+            if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+            return FG_OK;
+        }
     }
 
     // pass descriptors in dependency order per image, then items interleaved by rank
@@ -1577,7 +1665,12 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
     const size_t off_items = align256(off_desc + ndesc * sizeof(BatchDesc));
     const size_t off_cnt = align256(off_items + nitems * sizeof(BatchItem));
     const size_t off_bufs = align256(off_cnt + (1 + ndesc) * sizeof(int));
-    Workspace &ws = workspace_for(s);
+    Workspace &ws = wsb;
+    if (ws.batch.bytes < off_bufs + buf_total + 256) {
+        // cached graphs may point into the buffer about to be replaced
+        cudaStreamSynchronize(s);
+        clear_graphs(ws);
+    }
     if ((st = ensure(ws.batch, off_bufs + buf_total + 256, s)) != FG_OK) return st;
     char *dev = (char *)ws.batch.p;
 
@@ -1666,7 +1759,7 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
                 d.iters = passes[j];
                 d.dep = prev;
                 d.dep_count = prev >= 0 ? descs[prev].a.n_warps : 0;
-                if (plan_chunks(dtype, m.in, src, d.a, d.maps))
+                if (plan_chunks(dtype, m.in, src, d.a, d.maps, kBatchChunkCap))
                     chunk_max = std::max(chunk_max, d.a.tile_chunk);
                 else
                     planned = false;
@@ -1710,28 +1803,73 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
     std::memcpy(blob.data() + off_coarse, coarse.data(), n * sizeof(CoarseArgs));
     if (!descs.empty()) std::memcpy(blob.data() + off_desc, descs.data(), descs.size() * sizeof(BatchDesc));
     if (!items.empty()) std::memcpy(blob.data() + off_items, items.data(), items.size() * sizeof(BatchItem));
-    cudaError_t e = cudaMemcpyAsync(dev, blob.data(), blob.size(), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "copy of the batch work list");
-    if (!jobs.empty()) {
-        StageList L;
-        std::memset(&L, 0, sizeof L);
-        L.dev = reinterpret_cast<const StageJob *>(dev + off_jobs);
-        e = launch_stage_rows(dtype, L, (int)jobs.size(), stage_rows, s);
-        if (e != cudaSuccess) return cuda_fail(e, "row-aligned copies of the batch inputs");
+    // A graph cached for this batch keeps its own copy of the work list (descriptors, items,
+    // counters), so that another batch on this stream cannot overwrite it; the levels and
+    // staged copies stay in the shared workspace, which runs on this stream one batch at a time.
+    Buf own;
+    if (!key.empty() && cudaMalloc(&own.p, off_bufs) == cudaSuccess) {
+        own.bytes = off_bufs;
+    } else {
+        cudaGetLastError();
+        own.p = nullptr;
+        key.clear();
     }
-    e = launch_coarse_batch(dtype, p.clamp, reinterpret_cast<const CoarseArgs *>(dev + off_coarse), n,
-                            max_total, s);
-    if (e != cudaSuccess) return cuda_fail(e, "batched coarse kernel launch");
-    if (items.empty()) return FG_OK;
+    char *wl = own.p ? static_cast<char *>(own.p) : dev;
+    cudaError_t e = cudaMemcpyAsync(wl, blob.data(), blob.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        if (own.p) cudaFree(own.p);
+        return cuda_fail(e, "copy of the batch work list");
+    }
     BatchLaunch b;
-    b.descs = reinterpret_cast<const BatchDesc *>(dev + off_desc);
-    b.items = reinterpret_cast<const BatchItem *>(dev + off_items);
+    b.descs = reinterpret_cast<const BatchDesc *>(wl + off_desc);
+    b.items = reinterpret_cast<const BatchItem *>(wl + off_items);
     b.n_items = (int)items.size();
-    b.counters = reinterpret_cast<int *>(dev + off_cnt);
+    b.counters = reinterpret_cast<int *>(wl + off_cnt);
     b.wait_ns = kBatchWaitNs;
     b.slot_bytes = 0;
     b.region = region;   // 128-byte aligned, as the tensor copies into a warp's region require
-    return batch_launch(dtype, p.clamp, b, s);
+    // the launches of one batch call: counters cleared, row-aligned copies, coarse levels of
+    // every image, the work list
+    auto enqueue = [&](cudaStream_t q) -> fg_status {
+        cudaError_t e2 = cudaMemsetAsync(wl + off_cnt, 0, (1 + ndesc) * sizeof(int), q);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "clearing the work-list counters");
+        if (!jobs.empty()) {
+            StageList L;
+            std::memset(&L, 0, sizeof L);
+            L.dev = reinterpret_cast<const StageJob *>(wl + off_jobs);
+            e2 = launch_stage_rows(dtype, L, (int)jobs.size(), stage_rows, q);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "row-aligned copies of the batch inputs");
+        }
+        e2 = launch_coarse_batch(dtype, p.clamp, reinterpret_cast<const CoarseArgs *>(wl + off_coarse), n,
+                                 max_total, q);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "batched coarse kernel launch");
+        if (items.empty()) return FG_OK;
+        return batch_launch(dtype, p.clamp, b, q);
+    };
+    if (key.empty()) return enqueue(s);
+    cudaStream_t cs = capture_stream();
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    if (cs && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        st = enqueue(cs);
+        e = cudaStreamEndCapture(cs, &g);
+        if (st == FG_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&ex, g, 0);
+        if (g) cudaGraphDestroy(g);
+    }
+    if (!ex) {   // capture unavailable or refused: launch directly from the owned work list
+        cudaGetLastError();
+        st = enqueue(s);
+        cudaStreamSynchronize(s);
+        cudaFree(own.p);
+        return st;
+    }
+    evict_graphs(ws);
+    ws.graphs.emplace(key, ex);
+    ws.graph_order.push_back(key);
+    ws.graph_bufs.emplace(key, own);
+    e = cudaGraphLaunch(ex, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+    return FG_OK;
 }
 
 extern "C" fg_status fg_autotune_batch(int n, const fg_image *I, const fg_image *alpha,
@@ -1796,6 +1934,10 @@ extern "C" fg_status fg_selftest_bounded_wait(void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     Workspace &ws = workspace_for(s);
     const size_t off_item = align256(sizeof(BatchDesc)), off_cnt = off_item + 256;
+    if (ws.batch.bytes < off_cnt + 256) {
+        cudaStreamSynchronize(s);
+        clear_graphs(ws);   // cached batch graphs point into the buffer about to be replaced
+    }
     fg_status st = ensure(ws.batch, off_cnt + 256, s);
     if (st != FG_OK) return st;
     // one item that waits for its own pass: the count it waits for is never reached

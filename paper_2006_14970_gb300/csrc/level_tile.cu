@@ -39,63 +39,7 @@ __device__ int g_tile_error;
 
 namespace {
 
-constexpr unsigned kMask = 0xffffffffu;
-constexpr int kW = 60;             // output columns per warp
-constexpr int kWarps = 4;          // warps per block
-constexpr int kChunkRows = 4;      // rows per TMA gather (gather4)
-constexpr int kPolls = 1 << 20;    // try_wait polls before a wait gives up
-constexpr uint32_t kHintNs = 2000; // suspend-time hint of one poll
-#ifndef FGML_TILE_BLOCKS
-#define FGML_TILE_BLOCKS 3
-#endif
-
-using f2 = float2;
-__device__ __forceinline__ f2 mk(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-
-__device__ __forceinline__ uint32_t saddr(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Index v reflected into [0, n): -1 -> 0, -2 -> 1, n -> n - 1, n + 1 -> n - 2, clamped.
-__device__ __forceinline__ int reflect(int v, int n) {
-    if (v < 0) v = -1 - v;
-    if (v >= n) v = 2 * n - 1 - v;
-    return min(max(v, 0), n - 1);
-}
-
-// ------------------------------------------------------------------ loads and stores
-
-template <typename T> __device__ __forceinline__ float ldsh(const unsigned char *p);
-template <> __device__ __forceinline__ float ldsh<float>(const unsigned char *p) {
-    return *reinterpret_cast<const float *>(p);
-}
-template <> __device__ __forceinline__ float ldsh<__nv_bfloat16>(const unsigned char *p) {
-    return __uint_as_float((uint32_t)*reinterpret_cast<const unsigned short *>(p) << 16);
-}
-template <> __device__ __forceinline__ float ldsh<__half>(const unsigned char *p) {
-    return __half2float(*reinterpret_cast<const __half *>(p));
-}
-
-// The two 16-bit values of a 32-bit word as floats (low half first).
-__device__ __forceinline__ f2 unpack(uint32_t w, const __nv_bfloat16 *) {
-    return mk(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-}
-__device__ __forceinline__ f2 unpack(uint32_t w, const __half *) {
-    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
-}
-
-__device__ __forceinline__ void st_pair(__nv_bfloat16 *p, float a, float b) {
-    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
-}
-__device__ __forceinline__ void st_pair(__half *p, float a, float b) {
-    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
-}
-__device__ __forceinline__ void st_pair(float *p, float a, float b) {
-    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
-}
+#include "tile_common.cuh"
 
 // ------------------------------------------------------------------ per-lane state
 
@@ -107,7 +51,9 @@ struct FB {              // F and B of the lane's pixel pair, one float2 per cha
 struct Carry {
     f2 a;                // alpha of row r
     f2 a1;               // alpha of row r - 1 (compositing epilogue only)
-    f2 I[3];             // image of row r
+    f2 I[3];             // image of row r; after the row's first step, its data terms
+                         // alpha I (DF) and (1 - alpha) I (in DB)
+    f2 DB[3];
     float hl, hm, hr;    // row r's horizontal edge weights: left of p0, p0-p1, right of p1
     f2 sh;               // (hl + hm, hm + hr)
     f2 wu;               // row r's edge weights to row r - 1
@@ -126,10 +72,6 @@ struct Lane {
     bool vst;            // paired stores allowed (o0 && o1 and aligned)
     long long col;       // byte offset of p0 in an output row
 };
-
-__device__ __forceinline__ float edge(float ai, float aj, float eps, float omega) {
-    return fmaf(omega, fabsf(ai - aj), eps);
-}
 
 // Row data from the chunk in shared memory (row j of the slot at `slot`).
 template <typename T>
@@ -166,19 +108,18 @@ __device__ __forceinline__ void load_row(const PassArgs &p, const Lane &L,
     }
 }
 
-// Sums of a row: the data term U I, the neighbour above (weight wu) and the left/right
-// neighbours of X (shuffles; weights hl/hm/hr of the row).
-__device__ __forceinline__ void start_sums(f2 a, const f2 *I, f2 wu, const FB &up, const FB &X,
-                                           float hl, float hm, float hr, FB &acc) {
-    const f2 be = mk(1.f - a.x, 1.f - a.y);
+// Sums of a row: the data terms (DF = alpha I, DB = (1 - alpha) I), the neighbour above
+// (weight wu) and the left/right neighbours of X (shuffles; weights hl/hm/hr of the row).
+__device__ __forceinline__ void start_sums(const f2 *DF, const f2 *DB, f2 wu, const FB &up,
+                                           const FB &X, float hl, float hm, float hr, FB &acc) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float lF = __shfl_up_sync(kMask, X.F[k].y, 1);
         const float rF = __shfl_down_sync(kMask, X.F[k].x, 1);
         const float lB = __shfl_up_sync(kMask, X.B[k].y, 1);
         const float rB = __shfl_down_sync(kMask, X.B[k].x, 1);
-        f2 sF = fma2(wu, up.F[k], mul2(a, I[k]));
-        f2 sB = fma2(wu, up.B[k], mul2(be, I[k]));
+        f2 sF = fma2(wu, up.F[k], DF[k]);
+        f2 sB = fma2(wu, up.B[k], DB[k]);
         sF.x = fmaf(hl, lF, fmaf(hm, X.F[k].y, sF.x));
         sF.y = fmaf(hm, X.F[k].x, fmaf(hr, rF, sF.y));
         sB.x = fmaf(hl, lB, fmaf(hm, X.B[k].y, sB.x));
@@ -188,39 +129,31 @@ __device__ __forceinline__ void start_sums(f2 a, const f2 *I, f2 wu, const FB &u
     }
 }
 
-// Adds the neighbour below (weight wd) and solves: out = clamp(M acc).
+// Adds the neighbour below (weight wd) to a pixel pair's sums of the three channels and
+// solves: out = clamp(M acc), M = [[mFF, -mFB], [-mFB, mBB]].
 template <bool CLAMP>
-__device__ __forceinline__ void finish(FB &acc, f2 wd, const FB &dn, f2 mFF, f2 mBB, f2 mFB,
-                                       FB &out) {
+__device__ __forceinline__ void finish3(const f2 *aF, const f2 *aB, f2 wd, const f2 *dF, const f2 *dB,
+                                        f2 mFF, f2 mBB, f2 mFB, f2 *oF, f2 *oB) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const f2 sF = fma2(wd, dn.F[k], acc.F[k]);
-        const f2 sB = fma2(wd, dn.B[k], acc.B[k]);
+        const f2 sF = fma2(wd, dF[k], aF[k]);
+        const f2 sB = fma2(wd, dB[k], aB[k]);
         const f2 tF = mul2(mFB, sB);
         const f2 tB = mul2(mFB, sF);
         if (CLAMP) {
-            out.F[k] = mk(__saturatef(fmaf(mFF.x, sF.x, -tF.x)), __saturatef(fmaf(mFF.y, sF.y, -tF.y)));
-            out.B[k] = mk(__saturatef(fmaf(mBB.x, sB.x, -tB.x)), __saturatef(fmaf(mBB.y, sB.y, -tB.y)));
+            oF[k] = mk(__saturatef(fmaf(mFF.x, sF.x, -tF.x)), __saturatef(fmaf(mFF.y, sF.y, -tF.y)));
+            oB[k] = mk(__saturatef(fmaf(mBB.x, sB.x, -tB.x)), __saturatef(fmaf(mBB.y, sB.y, -tB.y)));
         } else {
-            out.F[k] = mk(fmaf(mFF.x, sF.x, -tF.x), fmaf(mFF.y, sF.y, -tF.y));
-            out.B[k] = mk(fmaf(mBB.x, sB.x, -tB.x), fmaf(mBB.y, sB.y, -tB.y));
+            oF[k] = mk(fmaf(mFF.x, sF.x, -tF.x), fmaf(mFF.y, sF.y, -tF.y));
+            oB[k] = mk(fmaf(mBB.x, sB.x, -tB.x), fmaf(mBB.y, sB.y, -tB.y));
         }
     }
 }
 
-// Inverse of A = [[a^2 + S, a(1-a)], [a(1-a), (1-a)^2 + S]] as (mFF, mBB, mFB) with
-// A^{-1} = [[mFF, -mFB], [-mFB, mBB]].
-__device__ __forceinline__ void invert(f2 a, f2 S, f2 &mFF, f2 &mBB, f2 &mFB) {
-    const f2 be = mk(1.f - a.x, 1.f - a.y);
-    const f2 A00 = fma2(a, a, S);
-    const f2 A11 = fma2(be, be, S);
-    const f2 A01 = mul2(a, be);
-    const f2 pd = mul2(A00, A11);
-    const float d0 = fmaf(-A01.x, A01.x, pd.x), d1 = fmaf(-A01.y, A01.y, pd.y);
-    const f2 m = mk(__fdividef(1.f, d0), __fdividef(1.f, d1));
-    mFF = mul2(A11, m);
-    mBB = mul2(A00, m);
-    mFB = mul2(A01, m);
+template <bool CLAMP>
+__device__ __forceinline__ void finish(const FB &acc, f2 wd, const FB &dn, f2 mFF, f2 mBB, f2 mFB,
+                                       FB &out) {
+    finish3<CLAMP>(acc.F, acc.B, wd, dn.F, dn.B, mFF, mBB, mFB, out.F, out.B);
 }
 
 template <typename T>
@@ -288,9 +221,18 @@ __device__ __forceinline__ void row_step(const PassArgs &p, const Lane &L, const
     cu.hl = __shfl_up_sync(kMask, cu.hr, 1);
     cu.sh = mk(cu.hl + cu.hm, cu.hm + cu.hr);
     cu.wu = mk(edge(cu.a.x, pv.a.x, eps, omega), edge(cu.a.y, pv.a.y, eps, omega));
+    {
+        // the row's data terms, used by both sweeps; cu.I holds alpha I from here on
+        const f2 be = mk(1.f - cu.a.x, 1.f - cu.a.y);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            cu.DB[k] = mul2(be, cu.I[k]);
+            cu.I[k] = mul2(cu.a, cu.I[k]);
+        }
+    }
     if (ST & kM) invert(pv.a, add2(add2(pv.sh, pv.wu), cu.wu), cu.mFF, cu.mBB, cu.mFB);
     if (ST & kS1) {
-        FB acc = pv.acc1;
+        const FB &acc = pv.acc1;
         if (K == 1) {
             FB out;
             finish<CLAMP>(acc, cu.wu, cu.Q, cu.mFF, cu.mBB, cu.mFB, out);
@@ -303,34 +245,20 @@ __device__ __forceinline__ void row_step(const PassArgs &p, const Lane &L, const
         }
     }
     if (K == 2 && (ST & kS2)) {
-        FB acc = pv.acc2, out;
-        finish<CLAMP>(acc, pv.wu, cu.P, pv.mFF, pv.mBB, pv.mFB, out);
+        FB out;
+        finish<CLAMP>(pv.acc2, pv.wu, cu.P, pv.mFF, pv.mBB, pv.mFB, out);
         if (r - 2 < Y1) {
             if (COMP) composite_row<T>(p, L, r - 2, out, pv.a1);
             store_row<T>(p, L, r - 2, out);
         }
     }
-    if (K == 2 && (ST & kA2)) start_sums(pv.a, pv.I, pv.wu, pv.P, cu.P, pv.hl, pv.hm, pv.hr, cu.acc2);
-    if (ST & kA1) start_sums(cu.a, cu.I, cu.wu, pv.Q, cu.Q, cu.hl, cu.hm, cu.hr, cu.acc1);
+    if (K == 2 && (ST & kA2)) start_sums(pv.I, pv.DB, pv.wu, pv.P, cu.P, pv.hl, pv.hm, pv.hr, cu.acc2);
+    if (ST & kA1) start_sums(cu.I, cu.DB, cu.wu, pv.Q, cu.Q, cu.hl, cu.hm, cu.hr, cu.acc1);
 }
 
 // ------------------------------------------------------------------ the kernel
 
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst), "l"(src) : "memory");
-}
 
-// The calling warp's chunk mbarriers: `n` of them at bar0, initialised once (arrival
-// count 1: lane 0's arrival that also sets the bytes the gathers deliver) and used by
-// every strip the warp runs; per-lane copies add their own arrivals before lane 0's.
-__device__ __forceinline__ void init_chunk_barriers(uint32_t bar0, int n) {
-    if ((threadIdx.x & 31) == 0) {
-        for (int s = 0; s < n; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar0 + 8u * s) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-}
 
 // One strip (`strip` of the pass) run by the calling warp, with its chunk slots at wbase
 // and their mbarriers at bar0 (p.tile_slots of each); `phase` holds the parity each
@@ -366,8 +294,8 @@ __device__ __forceinline__ bool tile_strip(const PassArgs &p, const CUtensorMap 
     // the lane's words at lane * (words per lane) * 4 (16-bit values keep their position
     // inside their 4-byte word).
     Lane L;
-    L.lane = lane;
     {
+        L.lane = lane;
         const int cI0 = 3 * gi0 * es, cI1 = 3 * gi1 * es, cA0 = gi0 * es, cA1 = gi1 * es;
         const int cS0 = 3 * gs0 * es, cS1 = 3 * gs1 * es;
         if (!LANES || p.lt_mode[0] == 0) {
@@ -420,6 +348,7 @@ __device__ __forceinline__ bool tile_strip(const PassArgs &p, const CUtensorMap 
     else bx = (3 * gsF * es) / 16 * (16 / p.tile_uS);
     const int doff = p.lt_off[limg];
 
+    int fslot = 0, tslot = 0;   // slots of the next chunk to fill and to take
     // Chunk c: rows R0 + 4c .. R0 + 4c + 3 (reflected into the image) into slot c % slots.
     // Lanes 0..7 each find one source row (lanes 0-3 of I and alpha, 4-7 of F and B).
     // With per-lane copies every lane first copies its own pixels' words of the four rows
@@ -433,7 +362,10 @@ __device__ __forceinline__ bool tile_strip(const PassArgs &p, const CUtensorMap 
         const int sel = lane >= 2 ? 4 : 0;
         const int y0 = __shfl_sync(kMask, v, sel + 0), y1 = __shfl_sync(kMask, v, sel + 1);
         const int y2 = __shfl_sync(kMask, v, sel + 2), y3 = __shfl_sync(kMask, v, sel + 3);
-        const int s = c % slots;
+        // slots are used in turn: fslot is chunk c's (c % slots, kept without a division)
+        const int s = fslot;
+        fslot = fslot + 1 == slots ? 0 : fslot + 1;
+        (void)c;
         const uint32_t bar = bar0 + 8u * (uint32_t)s;
         const uint32_t sbase = saddr(wbase + s * p.tile_chunk);
         // the slot's previous rows have been read by every lane (the caller synchronised
@@ -507,7 +439,9 @@ __device__ __forceinline__ bool tile_strip(const PassArgs &p, const CUtensorMap 
     };
     // Bounded wait for chunk c; false (and the device error word set) if it gave up.
     auto wait = [&](int c) -> bool {
-        const int b = c % slots;
+        const int b = tslot;   // chunk c's slot: chunks are taken in order
+        tslot = tslot + 1 == slots ? 0 : tslot + 1;
+        (void)c;
         const uint32_t bar = bar0 + 8u * (uint32_t)b;
         const uint32_t par = (phase >> b) & 1u;
         phase ^= 1u << b;
@@ -540,7 +474,6 @@ __device__ __forceinline__ bool tile_strip(const PassArgs &p, const CUtensorMap 
     {
         const unsigned char *slot = wbase;
         row_step<T, K, CLAMP, COMP, 0>(p, L, slot, 0, R0, Y1, C0, C0);   // pv unused
-        C0.wu = mk(p.eps, p.eps);
         row_step<T, K, CLAMP, COMP, kA1>(p, L, slot, 1, R0 + 1, Y1, C0, C1);
         if (K == 2) {
             row_step<T, K, CLAMP, COMP, kM | kS1 | kA1>(p, L, slot, 2, R0 + 2, Y1, C1, C0);
@@ -552,12 +485,14 @@ __device__ __forceinline__ bool tile_strip(const PassArgs &p, const CUtensorMap 
     }
     __syncwarp();
     if (filled < nchunks) fill(filled++);
+    int cslot = slots > 1 ? 1 : 0;   // slot of chunk c in the loop below
     for (int c = 1; c < nchunks; ++c) {
         if (!wait(c)) {
             abort(c, filled);
             return false;
         }
-        const unsigned char *slot = wbase + (c % slots) * p.tile_chunk;
+        const unsigned char *slot = wbase + cslot * p.tile_chunk;
+        cslot = cslot + 1 == slots ? 0 : cslot + 1;
         const int r = R0 + kChunkRows * c;
         row_step<T, K, CLAMP, COMP, kAll>(p, L, slot, 0, r, Y1, C1, C0);
         row_step<T, K, CLAMP, COMP, kAll>(p, L, slot, 1, r + 1, Y1, C0, C1);

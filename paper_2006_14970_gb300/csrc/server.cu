@@ -1,9 +1,10 @@
 // Serving loop: continuous batching of foreground-estimation jobs on one GPU.
 //
-// Callers submit jobs (host I and alpha, host F and B to fill) at any time. A scheduler
-// thread admits queued jobs in arrival order while a slot is free and the job's device
-// bytes fit in the server's HBM budget; admitted jobs get device buffers from the
-// stream-ordered allocator (no device-wide synchronisation), their inputs are copied up,
+// Callers submit jobs (I and alpha, F and B to fill; host or device memory) at any time. A
+// scheduler thread admits queued jobs in arrival order while a slot is free and the job's
+// device bytes fit in the server's HBM budget and in the device's free memory read at
+// that moment; admitted jobs get device buffers from the stream-ordered allocator (no
+// device-wide synchronisation), host inputs are copied up (device inputs read in place),
 // and every admitted job not yet launched is merged with the others of its dtype into
 // one fg_estimate_batch launch on the next idle compute stream. Jobs that arrive while
 // earlier batches run are admitted as soon as slots and memory free up and join the
@@ -52,6 +53,7 @@ struct Job {
     size_t bytes;            // device bytes reserved for the job
     Clock::time_point t_submit, t_done;
     void *dI = nullptr, *dA = nullptr, *dF = nullptr, *dB = nullptr;
+    cudaEvent_t inputs_ready = nullptr;   // the job's inputs are on the device
     int state = 0;           // 0 queued, 1 admitted, 2 launched, 3 done, 4 failed
     fg_status status = FG_OK;
     std::string error;
@@ -69,6 +71,9 @@ struct fg_server {
     fg_server_cfg cfg;
     int device = 0;
     std::vector<cudaStream_t> streams;
+    cudaStream_t up = nullptr;        // uploads of every job, in admission order
+    size_t free_headroom = 0;          // device memory free beyond the reserve, last read
+    Clock::time_point free_at{};       // when it was read
     std::vector<bool> busy;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -87,13 +92,20 @@ struct fg_server {
 
 namespace {
 
-// Device bytes a job holds while admitted: its I, alpha, F and B plus its share of the
-// intermediate levels (two buffers of the largest intermediate level, a quarter of the
-// image each for the paper's schedule) and slack for the work list.
+// Device bytes a job holds while admitted: the copies of host inputs and outputs it
+// needs (I and alpha, F and B), its share of the intermediate levels (two buffers of the
+// largest intermediate level, a quarter of the image each for the paper's schedule) and
+// slack for the work list.
 size_t job_bytes(const fg_request &r) {
     const size_t n = (size_t)r.w * r.h, es = esize(r.dtype);
-    return n * es * (3 + 1 + 3 + 3) + n * es * 3 + (1u << 20);
+    size_t b = n * es * 3 + (1u << 20);
+    if (!(r.flags & FG_REQ_DEVICE_INPUT)) b += n * es * (3 + 1);
+    if (!(r.flags & FG_REQ_DEVICE_OUTPUT)) b += n * es * (3 + 3);
+    return b;
 }
+
+// Device memory admission keeps free: 2 % of the device, at least 256 MiB.
+size_t reserve_bytes(size_t total) { return std::max<size_t>(total / 50, 256ull << 20); }
 
 void fail_job(Job &j, fg_status st, const std::string &msg) {
     j.status = st;
@@ -103,29 +115,82 @@ void fail_job(Job &j, fg_status st, const std::string &msg) {
 }
 
 void release(fg_server *s, Job &j, cudaStream_t st) {
-    if (j.dI) cudaFreeAsync(j.dI, st);
-    if (j.dA) cudaFreeAsync(j.dA, st);
-    if (j.dF) cudaFreeAsync(j.dF, st);
-    if (j.dB) cudaFreeAsync(j.dB, st);
+    const bool din = j.req.flags & FG_REQ_DEVICE_INPUT, dout = j.req.flags & FG_REQ_DEVICE_OUTPUT;
+    if (j.inputs_ready) {
+        cudaEventDestroy(j.inputs_ready);
+        j.inputs_ready = nullptr;
+    }
+    if (j.dI && !din) cudaFreeAsync(j.dI, st);
+    if (j.dA && !din) cudaFreeAsync(j.dA, st);
+    if (j.dF && !dout) cudaFreeAsync(j.dF, st);
+    if (j.dB && !dout) cudaFreeAsync(j.dB, st);
     j.dI = j.dA = j.dF = j.dB = nullptr;
     s->used -= j.bytes;
     s->inflight -= 1;
 }
 
-// Admit queued jobs while a slot and the budget allow; returns how many were admitted.
-int admit(fg_server *s, cudaStream_t up) {
+// Admit queued jobs while a slot, the budget and the device's free memory allow; returns
+// how many were admitted. Free memory is read again for every admission round, so memory
+// taken or released by other users of the device counts.
+int admit(fg_server *s) {
     int n = 0;
-    while (!s->queue.empty() && s->inflight < s->cfg.max_inflight_jobs &&
-           s->used + s->queue.front()->bytes <= (size_t)s->cfg.hbm_budget_bytes) {
+    if (s->queue.empty()) return 0;
+    // the device's free memory, read again at most once a millisecond; what this server
+    // allocated since the last read is taken off it
+    const Clock::time_point now = Clock::now();
+    if (s->free_at == Clock::time_point() || now - s->free_at > std::chrono::milliseconds(1)) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        const size_t reserve = reserve_bytes(total_b);
+        s->free_headroom = free_b > reserve ? free_b - reserve : 0;
+        s->free_at = now;
+    }
+    size_t &headroom = s->free_headroom;   // for new allocations
+    // nothing in flight that could free memory, and the next job does not fit what the
+    // device has free: fail it rather than wait for memory other users may never release
+    while (!s->queue.empty() && s->inflight == 0 && s->queue.front()->bytes > headroom) {
         std::shared_ptr<Job> j = s->queue.front();
         s->queue.pop_front();
+        fail_job(*j, FG_ERR_OOM, "job needs " + std::to_string(j->bytes) + " device bytes, " +
+                                     std::to_string(headroom) + " are free beyond the reserve");
+        s->stats.failed += 1;
+        s->cv_done.notify_all();
+    }
+    while (!s->queue.empty() && s->inflight < s->cfg.max_inflight_jobs &&
+           s->used + s->queue.front()->bytes <= (size_t)s->cfg.hbm_budget_bytes &&
+           s->queue.front()->bytes <= headroom) {
+        std::shared_ptr<Job> j = s->queue.front();
+        s->queue.pop_front();
+        headroom -= j->bytes;
+        cudaStream_t up = s->up;
         const size_t npx = (size_t)j->req.w * j->req.h, es = esize(j->req.dtype);
-        cudaError_t e = cudaMallocAsync(&j->dI, npx * 3 * es, up);
-        if (e == cudaSuccess) e = cudaMallocAsync(&j->dA, npx * es, up);
-        if (e == cudaSuccess) e = cudaMallocAsync(&j->dF, npx * 3 * es, up);
-        if (e == cudaSuccess) e = cudaMallocAsync(&j->dB, npx * 3 * es, up);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(j->dI, j->req.I, npx * 3 * es, cudaMemcpyHostToDevice, up);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(j->dA, j->req.alpha, npx * es, cudaMemcpyHostToDevice, up);
+        const bool din = j->req.flags & FG_REQ_DEVICE_INPUT, dout = j->req.flags & FG_REQ_DEVICE_OUTPUT;
+        cudaError_t e = cudaSuccess;
+        if (din) {
+            j->dI = const_cast<void *>(j->req.I);
+            j->dA = const_cast<void *>(j->req.alpha);
+        } else {
+            e = cudaMallocAsync(&j->dI, npx * 3 * es, up);
+            if (e == cudaSuccess) e = cudaMallocAsync(&j->dA, npx * es, up);
+        }
+        if (dout) {
+            j->dF = j->req.F;
+            j->dB = j->req.B;
+        } else {
+            if (e == cudaSuccess) e = cudaMallocAsync(&j->dF, npx * 3 * es, up);
+            if (e == cudaSuccess) e = cudaMallocAsync(&j->dB, npx * 3 * es, up);
+        }
+        if (e == cudaSuccess && !din) e = cudaMemcpyAsync(j->dI, j->req.I, npx * 3 * es, cudaMemcpyHostToDevice, up);
+        if (e == cudaSuccess && !din) e = cudaMemcpyAsync(j->dA, j->req.alpha, npx * es, cudaMemcpyHostToDevice, up);
+        // device inputs still being written elsewhere: the upload stream (which every
+        // batch waits for) waits for the caller's event
+        if (e == cudaSuccess && din && j->req.ready_event)
+            e = cudaStreamWaitEvent(up, static_cast<cudaEvent_t>(j->req.ready_event), 0);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->inputs_ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(j->inputs_ready, up);
         s->used += j->bytes;
         s->inflight += 1;
         if (e != cudaSuccess) {
@@ -146,7 +211,7 @@ int admit(fg_server *s, cudaStream_t up) {
 }
 
 // Launch the admitted jobs of one dtype as one batch on an idle stream.
-bool launch_batch(fg_server *s, cudaStream_t up) {
+bool launch_batch(fg_server *s) {
     if (s->admitted.empty()) return false;
     int k = -1;
     for (size_t i = 0; i < s->busy.size(); ++i)
@@ -167,12 +232,8 @@ bool launch_batch(fg_server *s, cudaStream_t up) {
     }
     s->admitted.swap(rest);
     cudaStream_t st = s->streams[k];
-    // inputs were copied on the upload stream; order the batch after them
-    cudaEvent_t ready;
-    cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-    cudaEventRecord(ready, up);
-    cudaStreamWaitEvent(st, ready, 0);
-    cudaEventDestroy(ready);
+    // the batch runs once its own jobs' inputs are on the device
+    for (auto &j : b.jobs) cudaStreamWaitEvent(st, j->inputs_ready, 0);
     const int n = (int)b.jobs.size();
     std::vector<fg_image> I(n), A(n), F(n), B(n);
     for (int i = 0; i < n; ++i) {
@@ -189,8 +250,10 @@ bool launch_batch(fg_server *s, cudaStream_t up) {
         Job &j = *b.jobs[i];
         const size_t npx = (size_t)j.req.w * j.req.h, es = esize(j.req.dtype);
         if (status == FG_OK) {
-            cudaMemcpyAsync(j.req.F, j.dF, npx * 3 * es, cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(j.req.B, j.dB, npx * 3 * es, cudaMemcpyDeviceToHost, st);
+            if (!(j.req.flags & FG_REQ_DEVICE_OUTPUT)) {
+                cudaMemcpyAsync(j.req.F, j.dF, npx * 3 * es, cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(j.req.B, j.dB, npx * 3 * es, cudaMemcpyDeviceToHost, st);
+            }
             j.state = 2;
         } else {
             j.status = status;
@@ -253,22 +316,21 @@ int retire(fg_server *s) {
 
 void worker_main(fg_server *s) {
     cudaSetDevice(s->device);
-    cudaStream_t up;
-    cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         const int done = retire(s);
         if (done) s->cv_done.notify_all();
-        admit(s, up);
-        while (launch_batch(s, up)) {
+        admit(s);
+        while (launch_batch(s)) {
         }
         if (s->stop && s->queue.empty() && s->admitted.empty() && s->running.empty()) break;
         // nothing to launch: sleep until a submission or a short poll interval passes
         s->cv_work.wait_for(lk, std::chrono::microseconds(s->running.empty() ? 2000 : 20));
     }
     lk.unlock();
-    cudaStreamSynchronize(up);
-    cudaStreamDestroy(up);
+    cudaStreamSynchronize(s->up);
+    cudaStreamDestroy(s->up);
 }
 
 double secs(const fg_server *s, Clock::time_point t) {
@@ -333,6 +395,10 @@ fg_status fg_server_submit(fg_server *s, const fg_request *r, uint64_t *ticket) 
         return sfail(FG_ERR_INVALID_ARG, "size %dx%d outside [1, 32767]", r->w, r->h);
     if (r->dtype != FG_F32 && r->dtype != FG_BF16 && r->dtype != FG_F16)
         return sfail(FG_ERR_INVALID_ARG, "unknown dtype");
+    if (r->flags & ~(FG_REQ_DEVICE_INPUT | FG_REQ_DEVICE_OUTPUT))
+        return sfail(FG_ERR_INVALID_ARG, "unknown request flags 0x%x", r->flags);
+    if ((r->flags & FG_REQ_DEVICE_INPUT) && ((uintptr_t)r->I % esize(r->dtype) || (uintptr_t)r->alpha % esize(r->dtype)))
+        return sfail(FG_ERR_INVALID_ARG, "device inputs are misaligned");
     auto j = std::make_shared<Job>();
     j->req = *r;
     j->bytes = job_bytes(*r);

@@ -363,10 +363,13 @@ class ServerCfg(ctypes.Structure):
                 ("streams", ctypes.c_int), ("max_batch", ctypes.c_int), ("params", Params)]
 
 
+FG_REQ_DEVICE_INPUT, FG_REQ_DEVICE_OUTPUT = 1, 2
+
+
 class Request(ctypes.Structure):
     _fields_ = [("I", ctypes.c_void_p), ("alpha", ctypes.c_void_p), ("w", ctypes.c_int),
                 ("h", ctypes.c_int), ("dtype", ctypes.c_int), ("F", ctypes.c_void_p),
-                ("B", ctypes.c_void_p)]
+                ("B", ctypes.c_void_p), ("flags", ctypes.c_int), ("ready_event", ctypes.c_void_p)]
 
 
 class ServerStats(ctypes.Structure):
@@ -434,24 +437,37 @@ class Server:
             raise FgmlError(st, self._lib.fg_server_last_error().decode())
 
     def submit(self, I: torch.Tensor, alpha: torch.Tensor, F=None, B=None) -> int:
+        """Queues a job. I and alpha may be host tensors or CUDA tensors of the server's
+        device (read in place; their contents must be complete on the current stream,
+        whose position is passed to the server as the job's ready event). F and B default
+        to tensors of I's kind; a CUDA F and B are written in place."""
         I = I.contiguous()
         alpha = alpha.contiguous()
         h, w = alpha.shape
+        if I.is_cuda != alpha.is_cuda:
+            raise ValueError("I and alpha must both be host or both be CUDA tensors")
         pin = I.is_pinned()
         if F is None:
-            F = torch.empty(I.shape, dtype=I.dtype, pin_memory=pin)
+            F = torch.empty_like(I) if I.is_cuda else torch.empty(I.shape, dtype=I.dtype, pin_memory=pin)
         if B is None:
-            B = torch.empty(I.shape, dtype=I.dtype, pin_memory=pin)
+            B = torch.empty_like(I) if I.is_cuda else torch.empty(I.shape, dtype=I.dtype, pin_memory=pin)
+        if F.is_cuda != B.is_cuda or not (F.is_contiguous() and B.is_contiguous()):
+            raise ValueError("F and B must both be host or both be CUDA tensors, contiguous")
+        flags = (FG_REQ_DEVICE_INPUT if I.is_cuda else 0) | (FG_REQ_DEVICE_OUTPUT if F.is_cuda else 0)
+        ev = None
+        if I.is_cuda:
+            ev = torch.cuda.Event()
+            ev.record()
         r = Request(I.data_ptr(), alpha.data_ptr(), w, h, _DTYPES[I.dtype], F.data_ptr(),
-                    B.data_ptr())
+                    B.data_ptr(), flags, ev.cuda_event if ev is not None else None)
         t = ctypes.c_uint64()
         self._check(self._lib.fg_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
-        self._keep[t.value] = (I, alpha, F, B)
+        self._keep[t.value] = (I, alpha, F, B, ev)
         return t.value
 
     def wait(self, ticket: int, timeout_ms: int = -1):
         self._check(self._lib.fg_server_wait(self._h, ticket, timeout_ms))
-        _, _, F, B = self._keep[ticket]
+        _, _, F, B, _ = self._keep[ticket]
         return F, B
 
     def poll(self, ticket: int) -> bool:

@@ -102,3 +102,45 @@ def test_server_latency_records(fgml):
             a, b = srv.times(x)
             assert 0 <= a <= b
             srv.release(x)
+
+
+def test_server_device_resident_inputs_and_outputs(fgml):
+    # jobs whose I and alpha are already in device memory are read in place; device F and
+    # B are written in place; host jobs run in the same mix
+    jobs = _jobs(9, 4, dtypes=(torch.float32, torch.bfloat16))
+    with fgml.Server(streams=2, max_batch=4) as srv:
+        tickets, kinds = [], []
+        for i, (I, A) in enumerate(jobs):
+            kind = i % 3   # 0: all device, 1: device inputs and host outputs, 2: all host
+            if kind == 0:
+                t = srv.submit(I.cuda(), A.cuda())
+            elif kind == 1:
+                t = srv.submit(I.cuda(), A.cuda(), torch.empty(I.shape, dtype=I.dtype).pin_memory(),
+                               torch.empty(I.shape, dtype=I.dtype).pin_memory())
+            else:
+                t = srv.submit(I, A)
+            tickets.append(t)
+            kinds.append(kind)
+        outs = [srv.wait(t, 60000) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    for (I, A), (F, B), kind in zip(jobs, outs, kinds):
+        assert F.is_cuda == (kind == 0)
+        Fa, Ba = _alone(fgml, I, A)
+        tol = TOL[I.dtype]
+        assert float((F.cpu().float() - Fa.float()).abs().max()) <= tol
+        assert float((B.cpu().float() - Ba.float()).abs().max()) <= tol
+
+
+def test_server_rejects_unknown_request_flags(fgml):
+    import ctypes
+    lib = fgml._server_lib()
+    with fgml.Server() as srv:
+        I = torch.zeros((8, 8, 3)).pin_memory()
+        A = torch.zeros((8, 8)).pin_memory()
+        r = fgml.Request(I.data_ptr(), A.data_ptr(), 8, 8, fgml.FG_F32, I.data_ptr(), I.data_ptr(),
+                         8, None)
+        t = ctypes.c_uint64()
+        st = lib.fg_server_submit(srv._h, ctypes.byref(r), ctypes.byref(t))
+        assert st == fgml.FG_ERR_INVALID_ARG
+        assert "flags" in lib.fg_server_last_error().decode()
