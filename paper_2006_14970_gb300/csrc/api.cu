@@ -2,6 +2,7 @@
 // the launch sequence of the multi-level method (Algorithm 1).
 #include "fgml.h"
 #include "fgml_internal.h"
+#include "serve_internal.h"
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -12,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <string>
@@ -158,33 +160,36 @@ struct Buf {
 struct Workspace {
     Buf lev[2];   // intermediate level states: F then B, each w x h x 3
     Buf stage;    // device staging of the host-memory entry point
-    Buf batch;    // work lists and per-image levels of fg_estimate_batch
+    Buf batch;    // per-image levels (and row-aligned copies) of fg_estimate_batch
+    Buf worklist; // device copy of the last directly launched work list
     Buf aux;      // per-block partial sums of fg_quality
     Buf cg;       // vectors of fg_minimiser_cg
     Buf check;    // counter of the optional input range check
     Buf align;    // copies of I and alpha with rows on the 16-byte grid (tensor maps need it)
-    // side stream and events of the L2 prefetch that runs beside the coarse levels
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
     // launch sequences of fg_estimate captured as CUDA graphs, by call signature
     std::map<std::string, cudaGraphExec_t> graphs;
     std::vector<std::string> graph_order;   // oldest first, for eviction
     // work lists owned by cached batch graphs (each graph reads its own copy)
     std::map<std::string, Buf> graph_bufs;
+    // batch signatures seen once: a batch is captured when it comes a second time, so
+    // one-off batches (a server's) never pay for a capture
+    std::vector<std::string> batch_seen;
 };
 
 constexpr size_t kMaxGraphs = 64;   // cached launch graphs per workspace
 
-void clear_graphs(Workspace &ws) {
+// The workspace of stream s drops its cached graphs; the work lists they own are freed in
+// stream order, after the launches already queued on s.
+void clear_graphs(Workspace &ws, cudaStream_t s) {
     for (auto &kv : ws.graphs) cudaGraphExecDestroy(kv.second);
     ws.graphs.clear();
     ws.graph_order.clear();
-    for (auto &kv : ws.graph_bufs) cudaFree(kv.second.p);   // waits for work still reading it
+    for (auto &kv : ws.graph_bufs) cudaFreeAsync(kv.second.p, s);
     ws.graph_bufs.clear();
 }
 
 // Drops the oldest cached graph (and the work list it owns) once the cache is full.
-void evict_graphs(Workspace &ws) {
+void evict_graphs(Workspace &ws, cudaStream_t s) {
     while (ws.graphs.size() >= kMaxGraphs) {
         const std::string k = ws.graph_order.front();
         cudaGraphExecDestroy(ws.graphs[k]);
@@ -192,7 +197,7 @@ void evict_graphs(Workspace &ws) {
         ws.graph_order.erase(ws.graph_order.begin());
         auto b = ws.graph_bufs.find(k);
         if (b != ws.graph_bufs.end()) {
-            cudaFree(b->second.p);
+            cudaFreeAsync(b->second.p, s);
             ws.graph_bufs.erase(b);
         }
     }
@@ -579,31 +584,11 @@ bool needs_stage(const Input &in, int es) {
     return es == 2 && !(words(in.I, in.I_pitch * es) && words(in.A, in.A_pitch * es));
 }
 
-// L2 prefetch of the input beside the latency-bound levels: the coarse and small levels
-// use few SMs and little bandwidth, so while they run a side stream prefetches I and alpha
-// into L2, and the first level pass of at least an eighth of the input's pixels (the
-// first that reads many input rows) waits for it. Only inputs that fit in half of L2.
-// FGML_PREFETCH=0 turns it off (read once per process).
-struct Prefetch {
-    cudaStream_t side;
-    cudaEvent_t fork, join;
-};
-constexpr long long kPrefetchMaxBytes = 64LL << 20;
-
-bool prefetch_enabled() {
-    static const bool on = [] {
-        const char *e = std::getenv("FGML_PREFETCH");
-        return !(e && *e == '0');
-    }();
-    return on;
-}
-
 // The kernels of one solve, enqueued on `s` (no allocation, no synchronisation).
 fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
                           const std::vector<Level> &lv, int nc, void *Fd, void *Bd,
                           long long d_pitch, Workspace &ws, int es, cudaStream_t s,
-                          const Composite *cmp = nullptr, const Input *staged_from = nullptr,
-                          const Prefetch *pf = nullptr) {
+                          const Composite *cmp = nullptr, const Input *staged_from = nullptr) {
     if (staged_from) {
         // I and alpha into their row-aligned copies (`in` describes the copies)
         const Input &o = *staged_from;
@@ -656,32 +641,14 @@ fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
         ca.Bd = (void *)src.B;
         ca.d_pitch = src.pitch;
     }
-    bool joined = true;
-    if (pf) {
-        const long long bI = ((long long)(in.h - 1) * in.I_pitch + 3LL * in.w) * es;
-        const long long bA = ((long long)(in.h - 1) * in.A_pitch + in.w) * es;
-        cudaError_t e = cudaEventRecord(pf->fork, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(pf->side, pf->fork, 0);
-        if (e == cudaSuccess) e = launch_prefetch_l2(in.I, bI, in.A, bA, pf->side);
-        if (e == cudaSuccess) e = cudaEventRecord(pf->join, pf->side);
-        if (e != cudaSuccess) return cuda_fail(e, "L2 prefetch of the input");
-        joined = false;
-    }
     cudaError_t e = launch_coarse(dtype, p.clamp, ca, s);
     if (e != cudaSuccess) return cuda_fail(e, "coarse kernel launch");
 
-    const long long npx = (long long)in.w * in.h;
     for (int l = nc; l < n; ++l) {
-        if (!joined && (long long)lv[l].w * lv[l].h * 8 >= npx) {
-            if ((e = cudaStreamWaitEvent(s, pf->join, 0)) != cudaSuccess) return cuda_fail(e, "joining the prefetch");
-            joined = true;
-        }
         fg_status st = run_level(dtype, p, in, src, buf, lv[l].k, lv[l].w, lv[l].h, l == n - 1,
                                  Fd, Bd, d_pitch, ws, es, s, l == n - 1 ? cmp : nullptr);
         if (st != FG_OK) return st;
     }
-    if (!joined && (e = cudaStreamWaitEvent(s, pf->join, 0)) != cudaSuccess)
-        return cuda_fail(e, "joining the prefetch");
     return FG_OK;
 }
 
@@ -733,7 +700,7 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
     if ((need && (ws.lev[0].bytes < need || ws.lev[1].bytes < need)) || ws.align.bytes < stage_need) {
         // cached graphs point at the buffers about to be replaced
         cudaStreamSynchronize(s);
-        clear_graphs(ws);
+        clear_graphs(ws, s);
         fg_status st = ensure(ws.lev[0], need, s);
         if (st != FG_OK) return st;
         st = ensure(ws.lev[1], need, s);
@@ -750,26 +717,8 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
         run.padded = true;
     }
     const Input *from = stage ? &in : nullptr;
-    // the input's L2 prefetch beside the coarse levels, for inputs that fit (not staged
-    // copies: those were just written and are in L2 already)
-    Prefetch pf{};
-    const Prefetch *pfp = nullptr;
-    const long long in_bytes = ((long long)(in.h - 1) * in.I_pitch + 3LL * in.w) * es +
-                               ((long long)(in.h - 1) * in.A_pitch + in.w) * es;
-    if (!stage && n > nc && in_bytes <= kPrefetchMaxBytes && prefetch_enabled()) {
-        if (!ws.side) {
-            if (cudaStreamCreateWithFlags(&ws.side, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&ws.fork, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&ws.join, cudaEventDisableTiming) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(FG_ERR_CUDA, "creating the prefetch stream and events");
-            }
-        }
-        pf = Prefetch{ws.side, ws.fork, ws.join};
-        pfp = &pf;
-    }
     if (!graphs_enabled())
-        return launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp, from, pfp);
+        return launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp, from);
 
     // the launch sequence depends on the pointers, pitches, sizes, dtype and parameters
     struct {
@@ -806,9 +755,9 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
         cudaStream_t cs = capture_stream();
         if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
-            return launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp, from, pfp);
+            return launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, s, cmp, from);
         }
-        fg_status st = launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, cs, cmp, from, pfp);
+        fg_status st = launch_sequence(run, dtype, p, lv, nc, Fd, Bd, d_pitch, ws, es, cs, cmp, from);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         if (st != FG_OK) {
@@ -820,7 +769,7 @@ fg_status estimate(const Input &in, int dtype, const fg_params &p, void *Fd, voi
         e = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(e, "instantiating the launch graph");
-        evict_graphs(ws);
+        evict_graphs(ws, s);
         it = ws.graphs.emplace(key, ex).first;
         ws.graph_order.push_back(key);
     }
@@ -1216,17 +1165,12 @@ fg_status fg_release_workspace(void *stream) {
         g_ws.erase(it);
     }
     cudaStreamSynchronize(s);
-    clear_graphs(w);
-    if (w.side) {
-        cudaStreamSynchronize(w.side);
-        cudaStreamDestroy(w.side);
-        cudaEventDestroy(w.fork);
-        cudaEventDestroy(w.join);
-    }
+    clear_graphs(w, s);
     cudaFree(w.lev[0].p);
     cudaFree(w.lev[1].p);
     cudaFree(w.stage.p);
     cudaFree(w.batch.p);
+    cudaFree(w.worklist.p);
     cudaFree(w.aux.p);
     cudaFree(w.cg.p);
     cudaFree(w.check.p);
@@ -1512,6 +1456,218 @@ fg_status batch_launch(int dtype, int clamp, BatchLaunch &b, cudaStream_t s) {
     return FG_OK;
 }
 
+// Bytes of each of the two buffers that hold an image's intermediate levels (0: none).
+size_t image_level_bytes(const std::vector<Level> &lv, int nc, int es) {
+    const int nl = (int)lv.size();
+    size_t need = 0;
+    if (nc < nl) need = state_bytes(lv[nc - 1].w, lv[nc - 1].h, es);
+    for (int l = nc; l < nl; ++l)
+        if (l != nl - 1 || split_sweeps(lv[l].k).size() > 1)
+            need = std::max(need, state_bytes(lv[l].w, lv[l].h, es));
+    return align256(need);
+}
+
+// One image's share of a work list: its coarse levels, then its level passes in order,
+// over intermediate-level buffers and outputs fixed when it is planned. Pass j reads what
+// pass j - 1 wrote (Algorithm 1: each level starts from the one below).
+struct ImagePlan {
+    CoarseArgs coarse;
+    std::vector<BatchDesc> passes;
+};
+
+// Plans image `in` (levels lv, the first nc in the coarse kernel) writing the finest
+// level to (Fd, Bd, d_pitch), with the intermediate levels ping-ponged in lev0 / lev1
+// (`need` bytes each). False when a 16-bit pass would need per-lane copies off the 4-byte
+// grid (no chunk layout); rows on the 16-byte grid always plan.
+bool plan_image(int dtype, const fg_params &p, const Input &in, const std::vector<Level> &lv, int nc,
+                void *Fd, void *Bd, long long d_pitch, void *lev0, void *lev1, size_t need,
+                ImagePlan &out) {
+    const int es = dtype == kF32 ? 4 : 2, nl = (int)lv.size();
+    Buf b0{lev0, need}, b1{lev1, need};
+    const Buf *bufs[2] = {&b0, &b1};
+    CoarseArgs &ca = out.coarse;
+    std::memset(&ca, 0, sizeof ca);
+    ca.I = in.I;
+    ca.I_pitch = in.I_pitch;
+    ca.A = in.A;
+    ca.A_pitch = in.A_pitch;
+    ca.Iw = in.w;
+    ca.Ih = in.h;
+    ca.nlev = nc;
+    for (int l = 0; l < nc; ++l) {
+        ca.lw[l] = lv[l].w;
+        ca.lh[l] = lv[l].h;
+        ca.lk[l] = lv[l].k;
+        ca.off[l] = ca.total;
+        ca.total += lv[l].w * lv[l].h;
+    }
+    ca.eps = p.eps_r;
+    ca.omega = p.omega;
+    ca.init = p.init;
+    State src{};
+    int buf = -1;
+    if (nc == nl) {
+        ca.Fd = Fd;
+        ca.Bd = Bd;
+        ca.d_pitch = d_pitch;
+    } else {
+        src = state_in(b0, lv[nc - 1].w, lv[nc - 1].h, es);
+        buf = 0;
+        ca.Fd = (void *)src.F;
+        ca.Bd = (void *)src.B;
+        ca.d_pitch = src.pitch;
+    }
+    out.passes.clear();
+    for (int l = nc; l < nl; ++l) {
+        const std::vector<int> sweeps = split_sweeps(lv[l].k);
+        for (size_t j = 0; j < sweeps.size(); ++j) {
+            const bool to_caller = l == nl - 1 && j + 1 == sweeps.size();
+            const int w = lv[l].w, h = lv[l].h;
+            void *F = Fd, *B = Bd;
+            long long dp = d_pitch;
+            State dst{};
+            int nb = buf;
+            if (!to_caller) {
+                nb = buf == 0 ? 1 : 0;
+                dst = state_in(*bufs[nb], w, h, es);
+                F = (void *)dst.F;
+                B = (void *)dst.B;
+                dp = dst.pitch;
+            }
+            BatchDesc d;
+            std::memset(&d, 0, sizeof d);
+            d.a = batch_pass_args(p, in, src, F, B, dp, w, h);
+            d.iters = sweeps[j];
+            d.dep = out.passes.empty() ? -1 : (int)out.passes.size() - 1;
+            d.dep_count = out.passes.empty() ? 0 : out.passes.back().a.n_warps;
+            if (!plan_chunks(dtype, in, src, d.a, d.maps, kBatchChunkCap)) return false;
+            out.passes.push_back(d);
+            if (!to_caller) {
+                src = dst;
+                buf = nb;
+            }
+        }
+    }
+    return true;
+}
+
+// A work list: the coarse launch's images, then the pass descriptors and their strips.
+struct WorkList {
+    std::vector<CoarseArgs> coarse;
+    std::vector<BatchDesc> descs;
+    std::vector<std::vector<int>> parts;   // descriptor indices of each part, in order
+    std::vector<BatchItem> items;
+    int max_total = 0, region = 0;
+};
+
+// Adds passes [first, last) of `plan`, and its coarse levels when with_coarse (run by the
+// coarse launch before the work list). Pass `first` waits for nothing: the passes before
+// it are done, in earlier launches or in this one's coarse launch.
+void worklist_add(WorkList &L, const ImagePlan &plan, bool with_coarse, int first, int last) {
+    if (with_coarse) {
+        L.coarse.push_back(plan.coarse);
+        L.max_total = std::max(L.max_total, plan.coarse.total);
+    }
+    std::vector<int> ix;
+    for (int j = first; j < last; ++j) {
+        BatchDesc d = plan.passes[j];
+        d.dep = ix.empty() ? -1 : ix.back();
+        d.dep_count = ix.empty() ? 0 : L.descs[ix.back()].a.n_warps;
+        ix.push_back((int)L.descs.size());
+        L.descs.push_back(d);
+    }
+    if (!ix.empty()) L.parts.push_back(std::move(ix));
+}
+
+// Every warp's region holds two chunks of the largest pass; smaller passes keep as many
+// chunks in flight as fit (at most three). Items are interleaved by rank (every part's
+// first pass, then every part's second ...), so that the strips a strip waits for were
+// all handed out before it.
+fg_status worklist_finish(WorkList &L) {
+    int chunk_max = 0;
+    for (const BatchDesc &d : L.descs) chunk_max = std::max(chunk_max, d.a.tile_chunk);
+    L.region = (2 * chunk_max + 127) & ~127;   // 128-byte aligned, as tensor copies into it require
+    if (L.region > kBatchRegionCap) return fail(FG_ERR_CUDA, "batch region %d exceeds the cap", L.region);
+    long long nitems = 0;
+    for (BatchDesc &d : L.descs) {
+        d.a.tile_slots = std::min(kBatchMaxSlots, L.region / std::max(1, d.a.tile_chunk));
+        nitems += d.a.n_warps;
+    }
+    if (nitems > (1LL << 30)) return fail(FG_ERR_INVALID_ARG, "batch too large");
+    L.items.clear();
+    L.items.reserve((size_t)nitems);
+    for (size_t rank = 0;; ++rank) {
+        bool any = false;
+        for (const std::vector<int> &part : L.parts) {
+            if (rank >= part.size()) continue;
+            any = true;
+            const int dix = part[rank];
+            for (int wi = 0; wi < L.descs[dix].a.n_warps; ++wi) L.items.push_back(BatchItem{dix, wi});
+        }
+        if (!any) break;
+    }
+    return FG_OK;
+}
+
+// Device copy of a work list: [row-aligned copy jobs][coarse args][descs][items][counters].
+struct WorkListLayout {
+    size_t off_jobs, off_coarse, off_desc, off_items, off_cnt, bytes;
+};
+
+WorkListLayout worklist_layout(const WorkList &L, size_t njobs) {
+    WorkListLayout o;
+    o.off_jobs = 0;
+    o.off_coarse = align256(njobs * sizeof(StageJob));
+    o.off_desc = align256(o.off_coarse + L.coarse.size() * sizeof(CoarseArgs));
+    o.off_items = align256(o.off_desc + L.descs.size() * sizeof(BatchDesc));
+    o.off_cnt = align256(o.off_items + L.items.size() * sizeof(BatchItem));
+    o.bytes = align256(o.off_cnt + (1 + L.descs.size()) * sizeof(int));
+    return o;
+}
+
+std::vector<char> worklist_blob(const WorkList &L, const std::vector<StageJob> &jobs,
+                                const WorkListLayout &o) {
+    std::vector<char> blob(o.bytes, 0);
+    if (!jobs.empty()) std::memcpy(blob.data() + o.off_jobs, jobs.data(), jobs.size() * sizeof(StageJob));
+    if (!L.coarse.empty())
+        std::memcpy(blob.data() + o.off_coarse, L.coarse.data(), L.coarse.size() * sizeof(CoarseArgs));
+    if (!L.descs.empty())
+        std::memcpy(blob.data() + o.off_desc, L.descs.data(), L.descs.size() * sizeof(BatchDesc));
+    if (!L.items.empty())
+        std::memcpy(blob.data() + o.off_items, L.items.data(), L.items.size() * sizeof(BatchItem));
+    return blob;
+}
+
+// The launches of one work list whose device copy is at `wl`: counters cleared, the
+// row-aligned copies, the coarse levels of its images, the strips.
+fg_status worklist_enqueue(int dtype, int clamp, const WorkList &L, const WorkListLayout &o,
+                           size_t njobs, long long stage_rows, char *wl, cudaStream_t q) {
+    cudaError_t e = cudaMemsetAsync(wl + o.off_cnt, 0, (1 + L.descs.size()) * sizeof(int), q);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the work-list counters");
+    if (njobs) {
+        StageList S;
+        std::memset(&S, 0, sizeof S);
+        S.dev = reinterpret_cast<const StageJob *>(wl + o.off_jobs);
+        e = launch_stage_rows(dtype, S, (int)njobs, stage_rows, q);
+        if (e != cudaSuccess) return cuda_fail(e, "row-aligned copies of the batch inputs");
+    }
+    if (!L.coarse.empty()) {
+        e = launch_coarse_batch(dtype, clamp, reinterpret_cast<const CoarseArgs *>(wl + o.off_coarse),
+                                (int)L.coarse.size(), L.max_total, q);
+        if (e != cudaSuccess) return cuda_fail(e, "batched coarse kernel launch");
+    }
+    if (L.items.empty()) return FG_OK;
+    BatchLaunch b;
+    b.descs = reinterpret_cast<const BatchDesc *>(wl + o.off_desc);
+    b.items = reinterpret_cast<const BatchItem *>(wl + o.off_items);
+    b.n_items = (int)L.items.size();
+    b.counters = reinterpret_cast<int *>(wl + o.off_cnt);
+    b.wait_ns = kBatchWaitNs;
+    b.slot_bytes = 0;
+    b.region = L.region;
+    return batch_launch(dtype, clamp, b, q);
+}
+
 }  // namespace
 
 extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image *alpha,
@@ -1563,7 +1719,6 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
     std::vector<Img> im(n);
     bool zero_sweeps = false;
     size_t buf_total = 0;
-    int nstage = 0;
     for (int i = 0; i < n; ++i) {
         Img &m = im[i];
         m.in = Input{I[i].ptr, alpha[i].ptr, I[i].row_pitch_bytes / es, alpha[i].row_pitch_bytes / es,
@@ -1572,14 +1727,9 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
         m.lv = plan_levels(m.in.w, m.in.h, p);
         m.nc = coarse_levels(m.lv);
         const int nl = (int)m.lv.size();
-        m.need = 0;
-        if (m.nc < nl) m.need = state_bytes(m.lv[m.nc - 1].w, m.lv[m.nc - 1].h, es);
-        for (int l = m.nc; l < nl; ++l) {
+        for (int l = m.nc; l < nl; ++l)
             if (m.lv[l].k == 0) zero_sweeps = true;
-            if (l != nl - 1 || split_sweeps(m.lv[l].k).size() > 1)
-                m.need = std::max(m.need, state_bytes(m.lv[l].w, m.lv[l].h, es));
-        }
-        m.need = align256(m.need);
+        m.need = image_level_bytes(m.lv, m.nc, es);
         m.buf_off = buf_total;
         buf_total += 2 * m.need;
         m.stage = m.nc < nl && needs_stage(m.in, es);
@@ -1589,8 +1739,6 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
             m.stage_off = buf_total;
             m.stage_offA = align256((size_t)(m.pI * es) * m.in.h);
             buf_total += m.stage_offA + align256((size_t)(m.pA * es) * m.in.h);
-            ++nstage;
-
         }
     }
     if (zero_sweeps || p.order != FG_ORDER_JACOBI) {
@@ -1636,53 +1784,33 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
             if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
             return FG_OK;
         }
+        auto seen = std::find(wsb.batch_seen.begin(), wsb.batch_seen.end(), key);
+        if (seen == wsb.batch_seen.end()) {   // first sight: launch directly, remember it
+            if (wsb.batch_seen.size() >= kMaxGraphs) wsb.batch_seen.erase(wsb.batch_seen.begin());
+            wsb.batch_seen.push_back(key);
+            key.clear();
+        } else {
+            wsb.batch_seen.erase(seen);
+        }
     }
 
-    // pass descriptors in dependency order per image, then items interleaved by rank
-    std::vector<CoarseArgs> coarse(n);
-    std::vector<BatchDesc> descs;
-    std::vector<std::vector<int>> per_image(n);
-    int max_total = 0;
-    // device layout: [coarse args][descs][items][counters][level buffers]; descs need the
-    // buffer addresses, so the blob is sized first and filled after allocation
-    std::vector<std::pair<int, int>> shape;   // (descs count, items count) found by a dry run
-    int ndesc = 0;
-    long long nitems = 0;
-    for (int i = 0; i < n; ++i)
-        for (int l = im[i].nc; l < (int)im[i].lv.size(); ++l)
-            for (int sweeps : split_sweeps(im[i].lv[l].k)) {
-                (void)sweeps;
-                ++ndesc;
-                const int w = im[i].lv[l].w, h = im[i].lv[l].h;
-                const int sh = batch_strip_rows(w, h);
-                nitems += (long long)((w + level_pass_strip_width() - 1) / level_pass_strip_width()) *
-                          ((h + sh - 1) / sh);
-            }
-    if (nitems > (1LL << 30)) return fail(FG_ERR_INVALID_ARG, "batch too large");
-    const size_t off_jobs = 0;
-    const size_t off_coarse = align256(off_jobs + 2 * nstage * sizeof(StageJob));
-    const size_t off_desc = align256(off_coarse + n * sizeof(CoarseArgs));
-    const size_t off_items = align256(off_desc + ndesc * sizeof(BatchDesc));
-    const size_t off_cnt = align256(off_items + nitems * sizeof(BatchItem));
-    const size_t off_bufs = align256(off_cnt + (1 + ndesc) * sizeof(int));
     Workspace &ws = wsb;
-    if (ws.batch.bytes < off_bufs + buf_total + 256) {
+    if (ws.batch.bytes < buf_total + 256) {
         // cached graphs may point into the buffer about to be replaced
         cudaStreamSynchronize(s);
-        clear_graphs(ws);
+        clear_graphs(ws, s);
     }
-    if ((st = ensure(ws.batch, off_bufs + buf_total + 256, s)) != FG_OK) return st;
-    char *dev = (char *)ws.batch.p;
+    if ((st = ensure(ws.batch, buf_total + 256, s)) != FG_OK) return st;
+    char *bufs = static_cast<char *>(ws.batch.p);
 
-    int chunk_max = 0;
-    bool planned = true;   // every pass has a chunk layout (else image by image)
     std::vector<StageJob> jobs;
     long long stage_rows = 0;
+    WorkList L;
+    ImagePlan plan;
     for (int i = 0; i < n; ++i) {
         Img &m = im[i];
-        const int nl = (int)m.lv.size();
         if (m.stage) {
-            char *sb = dev + off_bufs + m.stage_off;
+            char *sb = bufs + m.stage_off;
             Input c = m.in;
             c.I = sb;
             c.A = sb + m.stage_offA;
@@ -1697,173 +1825,55 @@ extern "C" fg_status fg_estimate_batch(int n, const fg_image *I, const fg_image 
             stage_rows += m.in.h;
             m.in = c;
         }
-        Buf b0{dev + off_bufs + m.buf_off, m.need}, b1{dev + off_bufs + m.buf_off + m.need, m.need};
-        const Buf *bufs[2] = {&b0, &b1};
-        CoarseArgs &ca = coarse[i];
-        std::memset(&ca, 0, sizeof ca);
-        ca.I = m.in.I;
-        ca.I_pitch = m.in.I_pitch;
-        ca.A = m.in.A;
-        ca.A_pitch = m.in.A_pitch;
-        ca.Iw = m.in.w;
-        ca.Ih = m.in.h;
-        ca.nlev = m.nc;
-        for (int l = 0; l < m.nc; ++l) {
-            ca.lw[l] = m.lv[l].w;
-            ca.lh[l] = m.lv[l].h;
-            ca.lk[l] = m.lv[l].k;
-            ca.off[l] = ca.total;
-            ca.total += m.lv[l].w * m.lv[l].h;
+        if (!plan_image(dtype, p, m.in, m.lv, m.nc, F[i].ptr, B[i].ptr, F[i].row_pitch_bytes / es,
+                        bufs + m.buf_off, bufs + m.buf_off + m.need, m.need, plan)) {
+            // a 16-bit pass whose rows would need per-lane copies off the 4-byte grid
+            for (int k = 0; k < n; ++k)
+                if ((st = estimate(im[k].orig, dtype, p, F[k].ptr, B[k].ptr, F[k].row_pitch_bytes / es, s)) != FG_OK)
+                    return st;
+            return FG_OK;
         }
-        ca.eps = p.eps_r;
-        ca.omega = p.omega;
-        ca.init = p.init;
-        max_total = std::max(max_total, ca.total);
-        State src{};
-        int buf = -1;
-        if (m.nc == nl) {
-            ca.Fd = F[i].ptr;
-            ca.Bd = B[i].ptr;
-            ca.d_pitch = F[i].row_pitch_bytes / es;
-        } else {
-            src = state_in(b0, m.lv[m.nc - 1].w, m.lv[m.nc - 1].h, es);
-            buf = 0;
-            ca.Fd = (void *)src.F;
-            ca.Bd = (void *)src.B;
-            ca.d_pitch = src.pitch;
-        }
-        int prev = -1;
-        for (int l = m.nc; l < nl; ++l) {
-            const std::vector<int> passes = split_sweeps(m.lv[l].k);
-            for (size_t j = 0; j < passes.size(); ++j) {
-                const bool to_caller = l == nl - 1 && j + 1 == passes.size();
-                const int w = m.lv[l].w, h = m.lv[l].h;
-                void *Fd, *Bd;
-                long long dp;
-                State dst{};
-                int nb = buf;
-                if (to_caller) {
-                    Fd = F[i].ptr;
-                    Bd = B[i].ptr;
-                    dp = F[i].row_pitch_bytes / es;
-                } else {
-                    nb = buf == 0 ? 1 : 0;
-                    dst = state_in(*bufs[nb], w, h, es);
-                    Fd = (void *)dst.F;
-                    Bd = (void *)dst.B;
-                    dp = dst.pitch;
-                }
-                BatchDesc d;
-                std::memset(&d, 0, sizeof d);
-                d.a = batch_pass_args(p, m.in, src, Fd, Bd, dp, w, h);
-                d.iters = passes[j];
-                d.dep = prev;
-                d.dep_count = prev >= 0 ? descs[prev].a.n_warps : 0;
-                if (plan_chunks(dtype, m.in, src, d.a, d.maps, kBatchChunkCap))
-                    chunk_max = std::max(chunk_max, d.a.tile_chunk);
-                else
-                    planned = false;
-                prev = (int)descs.size();
-                per_image[i].push_back(prev);
-                descs.push_back(d);
-                if (!to_caller) {
-                    src = dst;
-                    buf = nb;
-                }
-            }
-        }
+        worklist_add(L, plan, true, 0, (int)plan.passes.size());
     }
-    if (!planned) {
-        // a 16-bit pass whose rows would need per-lane copies off the 4-byte grid
-        for (int i = 0; i < n; ++i)
-            if ((st = estimate(im[i].orig, dtype, p, F[i].ptr, B[i].ptr, F[i].row_pitch_bytes / es, s)) != FG_OK)
-                return st;
-        return FG_OK;
-    }
-    // every warp's region holds two chunks of the largest pass; smaller passes keep as
-    // many chunks in flight as fit (at most three)
-    const int region = (2 * chunk_max + 127) & ~127;
-    if (region > kBatchRegionCap) return fail(FG_ERR_CUDA, "batch region %d exceeds the cap", region);
-    for (BatchDesc &d : descs) d.a.tile_slots = std::min(kBatchMaxSlots, region / std::max(1, d.a.tile_chunk));
-    std::vector<BatchItem> items;
-    items.reserve((size_t)nitems);
-    for (size_t rank = 0;; ++rank) {
-        bool any = false;
-        for (int i = 0; i < n; ++i) {
-            if (rank >= per_image[i].size()) continue;
-            any = true;
-            const int dix = per_image[i][rank];
-            for (int wi = 0; wi < descs[dix].a.n_warps; ++wi) items.push_back(BatchItem{dix, wi});
-        }
-        if (!any) break;
-    }
+    if ((st = worklist_finish(L)) != FG_OK) return st;
+    const WorkListLayout o = worklist_layout(L, jobs.size());
+    const std::vector<char> blob = worklist_blob(L, jobs, o);
 
-    std::vector<char> blob(off_bufs, 0);
-    if (!jobs.empty()) std::memcpy(blob.data() + off_jobs, jobs.data(), jobs.size() * sizeof(StageJob));
-    std::memcpy(blob.data() + off_coarse, coarse.data(), n * sizeof(CoarseArgs));
-    if (!descs.empty()) std::memcpy(blob.data() + off_desc, descs.data(), descs.size() * sizeof(BatchDesc));
-    if (!items.empty()) std::memcpy(blob.data() + off_items, items.data(), items.size() * sizeof(BatchItem));
     // A graph cached for this batch keeps its own copy of the work list (descriptors, items,
     // counters), so that another batch on this stream cannot overwrite it; the levels and
     // staged copies stay in the shared workspace, which runs on this stream one batch at a time.
     Buf own;
-    if (!key.empty() && cudaMalloc(&own.p, off_bufs) == cudaSuccess) {
-        own.bytes = off_bufs;
+    if (!key.empty() && cudaMallocAsync(&own.p, o.bytes, s) == cudaSuccess) {
+        own.bytes = o.bytes;
     } else {
         cudaGetLastError();
         own.p = nullptr;
         key.clear();
+        if ((st = ensure(ws.worklist, o.bytes, s)) != FG_OK) return st;
     }
-    char *wl = own.p ? static_cast<char *>(own.p) : dev;
+    char *wl = static_cast<char *>(own.p ? own.p : ws.worklist.p);
     cudaError_t e = cudaMemcpyAsync(wl, blob.data(), blob.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
-        if (own.p) cudaFree(own.p);
+        if (own.p) cudaFreeAsync(own.p, s);
         return cuda_fail(e, "copy of the batch work list");
     }
-    BatchLaunch b;
-    b.descs = reinterpret_cast<const BatchDesc *>(wl + off_desc);
-    b.items = reinterpret_cast<const BatchItem *>(wl + off_items);
-    b.n_items = (int)items.size();
-    b.counters = reinterpret_cast<int *>(wl + off_cnt);
-    b.wait_ns = kBatchWaitNs;
-    b.slot_bytes = 0;
-    b.region = region;   // 128-byte aligned, as the tensor copies into a warp's region require
-    // the launches of one batch call: counters cleared, row-aligned copies, coarse levels of
-    // every image, the work list
-    auto enqueue = [&](cudaStream_t q) -> fg_status {
-        cudaError_t e2 = cudaMemsetAsync(wl + off_cnt, 0, (1 + ndesc) * sizeof(int), q);
-        if (e2 != cudaSuccess) return cuda_fail(e2, "clearing the work-list counters");
-        if (!jobs.empty()) {
-            StageList L;
-            std::memset(&L, 0, sizeof L);
-            L.dev = reinterpret_cast<const StageJob *>(wl + off_jobs);
-            e2 = launch_stage_rows(dtype, L, (int)jobs.size(), stage_rows, q);
-            if (e2 != cudaSuccess) return cuda_fail(e2, "row-aligned copies of the batch inputs");
-        }
-        e2 = launch_coarse_batch(dtype, p.clamp, reinterpret_cast<const CoarseArgs *>(wl + off_coarse), n,
-                                 max_total, q);
-        if (e2 != cudaSuccess) return cuda_fail(e2, "batched coarse kernel launch");
-        if (items.empty()) return FG_OK;
-        return batch_launch(dtype, p.clamp, b, q);
-    };
-    if (key.empty()) return enqueue(s);
+    if (key.empty()) return worklist_enqueue(dtype, p.clamp, L, o, jobs.size(), stage_rows, wl, s);
     cudaStream_t cs = capture_stream();
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ex = nullptr;
     if (cs && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        st = enqueue(cs);
+        st = worklist_enqueue(dtype, p.clamp, L, o, jobs.size(), stage_rows, wl, cs);
         e = cudaStreamEndCapture(cs, &g);
         if (st == FG_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&ex, g, 0);
         if (g) cudaGraphDestroy(g);
     }
     if (!ex) {   // capture unavailable or refused: launch directly from the owned work list
         cudaGetLastError();
-        st = enqueue(s);
-        cudaStreamSynchronize(s);
-        cudaFree(own.p);
+        st = worklist_enqueue(dtype, p.clamp, L, o, jobs.size(), stage_rows, wl, s);
+        cudaFreeAsync(own.p, s);
         return st;
     }
-    evict_graphs(ws);
+    evict_graphs(ws, s);
     ws.graphs.emplace(key, ex);
     ws.graph_order.push_back(key);
     ws.graph_bufs.emplace(key, own);
@@ -1896,8 +1906,9 @@ extern "C" fg_status fg_autotune_batch(int n, const fg_image *I, const fg_image 
             std::lock_guard<std::mutex> lk(g_strips_mu);
             g_strips = kStripCandidates[c];
         }
-        // one untimed call (workspace growth), then two timed ones
-        st = fg_estimate_batch(n, I, alpha, params, F, B, stream);
+        // two untimed calls (workspace growth; the second captures the batch's graph),
+        // then two timed ones
+        for (int r = 0; r < 2 && st == FG_OK; ++r) st = fg_estimate_batch(n, I, alpha, params, F, B, stream);
         if (st != FG_OK) break;
         cudaEventRecord(e0, s);
         for (int r = 0; r < 2 && st == FG_OK; ++r) st = fg_estimate_batch(n, I, alpha, params, F, B, stream);
@@ -1936,7 +1947,7 @@ extern "C" fg_status fg_selftest_bounded_wait(void *stream) {
     const size_t off_item = align256(sizeof(BatchDesc)), off_cnt = off_item + 256;
     if (ws.batch.bytes < off_cnt + 256) {
         cudaStreamSynchronize(s);
-        clear_graphs(ws);   // cached batch graphs point into the buffer about to be replaced
+        clear_graphs(ws, s);   // cached batch graphs point into the buffer about to be replaced
     }
     fg_status st = ensure(ws.batch, off_cnt + 256, s);
     if (st != FG_OK) return st;
@@ -1972,3 +1983,70 @@ extern "C" fg_status fg_selftest_bounded_wait(void *stream) {
     if (code != 2) return fail(FG_ERR_CUDA, "the bounded wait did not report a timeout (code %d)", code);
     return fail(FG_ERR_TIMEOUT, "bounded wait gave up as intended");
 }
+
+// ====================================================== level-granular serving support
+
+namespace fgml {
+
+struct ServePlan {
+    ImagePlan image;
+    std::vector<long long> work;   // pixels x sweeps of each pass
+};
+
+size_t serve_level_bytes(int w, int h, int dtype, const fg_params &p) {
+    const std::vector<Level> lv = plan_levels(w, h, p);
+    return image_level_bytes(lv, coarse_levels(lv), dtype == kF32 ? 4 : 2);
+}
+
+bool serve_supported(const fg_params &p) {
+    return p.order == FG_ORDER_JACOBI && p.small_iters > 0 && p.big_iters > 0;
+}
+
+fg_status serve_plan_create(int dtype, const fg_params &p, const void *I, long long I_pitch,
+                            const void *A, long long A_pitch, bool padded, int w, int h, void *F,
+                            void *B, long long d_pitch, void *lev0, void *lev1, ServePlan **out) {
+    g_err.clear();
+    const int es = dtype == kF32 ? 4 : 2;
+    if (!rows_on_grid(I, I_pitch * es) || !rows_on_grid(A, A_pitch * es))
+        return fail(FG_ERR_INVALID_ARG, "serving plans need I and alpha rows on the 16-byte grid");
+    Input in{I, A, I_pitch, A_pitch, w, h};
+    in.padded = padded;
+    const std::vector<Level> lv = plan_levels(w, h, p);
+    const int nc = coarse_levels(lv);
+    std::unique_ptr<ServePlan> sp(new ServePlan());
+    if (!plan_image(dtype, p, in, lv, nc, F, B, d_pitch, lev0, lev1, image_level_bytes(lv, nc, es),
+                    sp->image))
+        return fail(FG_ERR_CUDA, "no chunk layout for a %dx%d job", w, h);
+    for (const BatchDesc &d : sp->image.passes) sp->work.push_back((long long)d.a.w * d.a.h * d.iters);
+    *out = sp.release();
+    return FG_OK;
+}
+
+void serve_plan_destroy(ServePlan *plan) { delete plan; }
+
+int serve_plan_passes(const ServePlan *plan) { return (int)plan->image.passes.size(); }
+
+long long serve_plan_work(const ServePlan *plan, int j) { return plan->work[j]; }
+
+fg_status serve_reserve(cudaStream_t s, size_t worklist_bytes) {
+    return ensure(workspace_for(s).worklist, worklist_bytes, s);
+}
+
+fg_status serve_launch(int dtype, const fg_params &p, const ServePart *parts, int n, cudaStream_t s) {
+    g_err.clear();
+    WorkList L;
+    for (int i = 0; i < n; ++i)
+        worklist_add(L, parts[i].plan->image, parts[i].coarse != 0, parts[i].first, parts[i].last);
+    fg_status st = worklist_finish(L);
+    if (st != FG_OK) return st;
+    const WorkListLayout o = worklist_layout(L, 0);
+    const std::vector<char> blob = worklist_blob(L, {}, o);
+    Workspace &ws = workspace_for(s);
+    if ((st = ensure(ws.worklist, o.bytes, s)) != FG_OK) return st;
+    char *wl = static_cast<char *>(ws.worklist.p);
+    cudaError_t e = cudaMemcpyAsync(wl, blob.data(), blob.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of the serving work list");
+    return worklist_enqueue(dtype, p.clamp, L, o, 0, 0, wl, s);
+}
+
+}  // namespace fgml

@@ -134,10 +134,6 @@ struct StageList {
 cudaError_t launch_stage_rows(int dtype, const StageList &list, int njobs, long long total_rows,
                               cudaStream_t s);
 
-// Prefetches the byte ranges [p0, p0 + n0) and [p1, p1 + n1) into L2 (the 16-byte aligned
-// interior of each; a null pointer or n <= 0 skips a range).
-cudaError_t launch_prefetch_l2(const void *p0, long long n0, const void *p1, long long n1,
-                               cudaStream_t s);
 
 // Adds to *bad (device) the number of values of a w x h x ch image (pitch in elements)
 // outside [0, 1] or NaN (the optional input check).

@@ -108,46 +108,3 @@ cudaError_t launch_range_check(int dtype, const void *p, long long pitch, int w,
 }
 
 }  // namespace fgml
-
-namespace fgml {
-namespace {
-
-constexpr int kPrefetchPiece = 16 << 10;   // bytes per bulk L2 prefetch
-
-// L2 prefetch of up to two byte ranges: each thread issues bulk prefetches of 32 KB
-// pieces (the last piece shorter), over the 16-byte aligned interior of each range.
-__global__ void __launch_bounds__(32) prefetch_l2_kernel(const char *p0, long long n0,
-                                                          const char *p1, long long n1) {
-    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long nthreads = (long long)gridDim.x * blockDim.x;
-    for (int r = 0; r < 2; ++r) {
-        const char *p = r == 0 ? p0 : p1;
-        const long long n = r == 0 ? n0 : n1;
-        if (!p || n <= 0) continue;
-        const uintptr_t lo = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
-        const uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + (uintptr_t)n) & ~(uintptr_t)15;
-        if (hi <= lo) continue;
-        const long long bytes = (long long)(hi - lo);
-        const long long pieces = (bytes + kPrefetchPiece - 1) / kPrefetchPiece;
-        for (long long k = tid; k < pieces; k += nthreads) {
-            const long long off = k * kPrefetchPiece;
-            const unsigned len = (unsigned)min((long long)kPrefetchPiece, bytes - off);
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(lo + off), "r"(len) : "memory");
-        }
-    }
-}
-
-}  // namespace
-
-cudaError_t launch_prefetch_l2(const void *p0, long long n0, const void *p1, long long n1,
-                               cudaStream_t s) {
-    // one piece per thread over up to 128 SMs' copy engines (the levels running beside the
-    // prefetch use few SMs)
-    const long long pieces = (n0 + n1) / kPrefetchPiece + 2;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>(128, (pieces + 31) / 32));
-    prefetch_l2_kernel<<<blocks, 32, 0, s>>>(static_cast<const char *>(p0), n0,
-                                             static_cast<const char *>(p1), n1);
-    return cudaGetLastError();
-}
-
-}  // namespace fgml

@@ -84,6 +84,40 @@ def test_batch_replay_reads_new_contents_and_keeps_its_own_work_list(fgml):
         assert np.abs(B.cpu().numpy() - Bo).max() <= TOL
 
 
+def test_batch_replay_reads_new_contents_and_keeps_its_own_work_list(fgml):
+    # a batch seen a second time (same buffers) is captured and then replayed: it must read
+    # what the buffers hold now, and two batches alternating on one stream must not share
+    # work lists
+    ss1 = _samples([(300, 211), (1939, 611), (64, 64)], 900)
+    ss2 = _samples([(517, 389), (128, 1024)], 910)
+    new1 = _samples([(300, 211), (1939, 611), (64, 64)], 920)
+    imgs1 = [(_dev(s.I), _dev(s.alpha)) for s in ss1]
+    imgs2 = [(_dev(s.I), _dev(s.alpha)) for s in ss2]
+    out1 = [(torch.empty_like(I), torch.empty_like(I)) for I, _ in imgs1]
+    out2 = [(torch.empty_like(I), torch.empty_like(I)) for I, _ in imgs2]
+    for rep in range(3):
+        fgml.estimate_batch(imgs1, outputs=out1)
+        fgml.estimate_batch(imgs2, outputs=out2)
+    fgml.sync()
+    for (F, B), s in zip(out1 + out2, ss1 + ss2):
+        Fo, Bo = oracle.ml(s.I, s.alpha)
+        assert np.abs(F.cpu().numpy() - Fo).max() <= TOL
+        assert np.abs(B.cpu().numpy() - Bo).max() <= TOL
+    # new contents in the same input buffers, outputs poisoned first
+    for (I, A), s in zip(imgs1, new1):
+        I.copy_(_dev(s.I))
+        A.copy_(_dev(s.alpha))
+    for F, B in out1:
+        F.fill_(float("nan"))
+        B.fill_(float("nan"))
+    fgml.estimate_batch(imgs1, outputs=out1)
+    fgml.sync()
+    for (F, B), s in zip(out1, new1):
+        Fo, Bo = oracle.ml(s.I, s.alpha)
+        assert np.abs(F.cpu().numpy() - Fo).max() <= TOL
+        assert np.abs(B.cpu().numpy() - Bo).max() <= TOL
+
+
 @pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
 def test_batch_reduced_precision_within_bound(fgml, dt):
     # each level's F and B are rounded to the storage type, so the batch and the
