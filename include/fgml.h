@@ -240,14 +240,19 @@ fg_status fg_selftest_bounded_wait(void *stream);
 
 /* ------------------------------------------------------------------ serving
  * A server runs jobs submitted at any time with continuous batching on the current
- * device: a scheduler thread admits queued jobs in arrival order while a slot is free and
+ * device. A scheduler thread admits queued jobs in arrival order while a slot is free and
  * the job's device bytes fit in the HBM budget and the device's free memory at that
- * moment, copies host inputs up (device inputs are read in place), merges every
- * admitted job not yet launched (of one dtype) into one fg_estimate_batch launch on an
- * idle compute stream, and completes jobs as their batch finishes (outputs copied back
- * to the job's host buffers). Jobs arriving while batches run join the next batch as
- * slots and memory free up, and that batch overlaps the running ones on the device. The
- * paper has no serving layer; the method run for each job is Algorithm 1.
+ * moment; an admitted job's pyramid (its intermediate levels) stays device-resident until
+ * it completes. Host inputs are copied up and host outputs back in pieces of at most 8 MB,
+ * the job with the fewest bytes left first (device inputs on the 16-byte row grid are read
+ * in place). Each launch merges the next level passes of every admitted job (of one dtype)
+ * whose inputs are on the device and that no running launch holds, up to step_work
+ * pixel-sweeps, into one work list on an idle compute stream, so a large job advances level
+ * by level across launches while later jobs join the next launches on the other streams.
+ * A job completes when its last pass is done and its outputs are in place. The paper has
+ * no serving layer; the method run for each job is Algorithm 1. Parameter sets the work
+ * list does not run (red-black order, a level without sweeps) are served whole jobs per
+ * launch.
  */
 typedef struct fg_server fg_server;
 
@@ -257,8 +262,10 @@ typedef struct {
                                     creation); admission also keeps what jobs hold below the
                                     device's free memory read at that moment, less a reserve */
     int streams;                 /* batches in flight at most, 1..16 (default 2) */
-    int max_batch;               /* jobs per batch at most (default 64) */
+    int max_batch;               /* jobs per launch at most (default 64) */
     fg_params params;            /* method parameters for every job */
+    long long step_work;         /* pixel-sweeps of level passes per launch at most (<= 0:
+                                    default 16 Mi); a single larger pass runs alone */
 } fg_server_cfg;
 
 typedef struct {

@@ -374,7 +374,8 @@ def estimate_noalloc(I: torch.Tensor, alpha: torch.Tensor, p: Params | None = No
 
 class ServerCfg(ctypes.Structure):
     _fields_ = [("max_inflight_jobs", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_longlong),
-                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int), ("params", Params)]
+                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int), ("params", Params),
+                ("step_work", ctypes.c_longlong)]
 
 
 FG_REQ_DEVICE_INPUT, FG_REQ_DEVICE_OUTPUT = 1, 2
@@ -424,12 +425,14 @@ def _server_lib():
 
 
 class Server:
-    """fg_server: continuous-batching job server on the current device. Jobs are host
-    tensors (I [H, W, 3], alpha [H, W], one float dtype); outputs are host tensors filled
-    when the job completes. Keep the tensors alive until then."""
+    """fg_server: continuous-batching job server on the current device, scheduled by level
+    pass (each launch merges the next passes of every admitted job, up to step_work
+    pixel-sweeps). Jobs are tensors (I [H, W, 3], alpha [H, W], one float dtype) in host or
+    device memory; outputs are filled when the job completes. Keep the tensors alive until
+    then."""
 
     def __init__(self, max_inflight_jobs=256, hbm_budget_bytes=0, streams=2, max_batch=64,
-                 p: Params | None = None):
+                 p: Params | None = None, step_work: int = 0):
         lib = _server_lib()
         cfg = ServerCfg()
         lib.fg_server_cfg_default(ctypes.byref(cfg))
@@ -437,6 +440,8 @@ class Server:
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.streams = streams
         cfg.max_batch = max_batch
+        if step_work > 0:
+            cfg.step_work = step_work
         if p is not None:
             cfg.params = p
         h = ctypes.c_void_p()

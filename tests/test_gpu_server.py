@@ -144,3 +144,70 @@ def test_server_rejects_unknown_request_flags(fgml):
         st = lib.fg_server_submit(srv._h, ctypes.byref(r), ctypes.byref(t))
         assert st == fgml.FG_ERR_INVALID_ARG
         assert "flags" in lib.fg_server_last_error().decode()
+
+
+def test_server_large_job_advances_by_levels_beside_small_jobs(fgml):
+    # a 4000x3000 job is split into several launches (its level passes, a few at a time);
+    # small jobs submitted right after it are copied up between its pieces, run in launches
+    # of their own and complete before it
+    big = synth.make_sample(4000, 3000, 3500)
+    Ib = torch.from_numpy(big.I).pin_memory()
+    Ab = torch.from_numpy(big.alpha).pin_memory()
+    Fb, Bb = torch.empty_like(Ib).pin_memory(), torch.empty_like(Ib).pin_memory()
+    small = _jobs(12, 5, lo=64, hi=256, dtypes=(torch.float32,))
+    outs = [(torch.empty_like(I).pin_memory(), torch.empty_like(I).pin_memory()) for I, _ in small]
+    with fgml.Server(streams=2, max_batch=16, step_work=4 << 20) as srv:
+        # first use of the server's pool and kernels, outside the timed scenario
+        for t in [srv.submit(Ib, Ab, Fb, Bb)] + [srv.submit(I, A, F, B) for (I, A), (F, B) in zip(small, outs)]:
+            srv.wait(t, 60000)
+        st0 = srv.stats()
+        tb = srv.submit(Ib, Ab, Fb, Bb)
+        ts = [srv.submit(I, A, F, B) for (I, A), (F, B) in zip(small, outs)]
+        for t in ts + [tb]:
+            srv.wait(t, 60000)
+        done_small = max(srv.times(t)[1] for t in ts)
+        done_big = srv.times(tb)[1]
+        st = srv.stats()
+    assert st["completed"] == 2 * (len(small) + 1) and st["failed"] == 0
+    assert st["batches"] - st0["batches"] >= 4
+    assert done_small < done_big
+    Fa, Ba = _alone(fgml, Ib, Ab)
+    assert float((Fb - Fa).abs().max()) <= TOL[torch.float32]
+    assert float((Bb - Ba).abs().max()) <= TOL[torch.float32]
+    for (I, A), (F, B) in zip(small, outs):
+        Fa, Ba = _alone(fgml, I, A)
+        assert float((F - Fa).abs().max()) <= TOL[torch.float32]
+        assert float((B - Ba).abs().max()) <= TOL[torch.float32]
+
+
+def test_server_one_pass_per_launch(fgml):
+    # a budget below every pass: each launch runs one pass of one job, so every pass
+    # after the first of a job starts from a state another launch wrote
+    jobs = _jobs(5, 6, lo=200, hi=400, dtypes=(torch.float32, torch.bfloat16))
+    with fgml.Server(streams=3, max_batch=8, step_work=1) as srv:
+        tickets = [srv.submit(I, A) for I, A in jobs]
+        outs = [srv.wait(t, 60000) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    assert st["batches"] >= 3 * len(jobs)   # every job has at least three level passes
+    for (I, A), (F, B) in zip(jobs, outs):
+        Fa, Ba = _alone(fgml, I, A)
+        tol = TOL[I.dtype]
+        assert float((F.float() - Fa.float()).abs().max()) <= tol
+        assert float((B.float() - Ba.float()).abs().max()) <= tol
+
+
+def test_server_red_black_runs_whole_jobs(fgml):
+    # the work list runs the Jacobi order only: a red-black server launches whole jobs
+    p = fgml.params(order=fgml.FG_ORDER_REDBLACK)
+    jobs = _jobs(6, 7, lo=100, hi=500, dtypes=(torch.float32,))
+    with fgml.Server(streams=2, max_batch=4, p=p) as srv:
+        tickets = [srv.submit(I, A) for I, A in jobs]
+        outs = [srv.wait(t, 60000) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    for (I, A), (F, B) in zip(jobs, outs):
+        Fa, Ba = fgml.estimate(I.cuda(), A.cuda(), p)
+        torch.cuda.synchronize()
+        assert float((F - Fa.cpu()).abs().max()) <= TOL[torch.float32]
+        assert float((B - Ba.cpu()).abs().max()) <= TOL[torch.float32]
