@@ -267,7 +267,7 @@ def serving_section(fgml, synth, torch, args):
     out = {"workload": "serving_poisson_256_4096_mixed_f32_bf16",
            "one_at_a_time_f32": {"req_s": cap_req, "mpix_s": cap_px / 1e6, "calls": calls,
                                  "seconds": dt1},
-           "rates": [], "bf16_only": []}
+           "rates": [], "bf16_only": [], "device_rates": []}
     mixed = []
     for i, (s, n) in enumerate(base):
         dt = torch.float32 if i % 2 == 0 else torch.bfloat16
@@ -279,9 +279,9 @@ def serving_section(fgml, synth, torch, args):
         bf16.append((I, A, n, outputs(I)))
     n_req = max(16, args.serving_requests)
 
-    def sweep(templates, rates, key):
+    def sweep(templates, rates, key, cap=None):
         for x in rates:
-            rate = x * cap_req
+            rate = x * (cap or cap_req)
             gaps = rng.exponential(1.0 / rate, n_req)
             picks = rng.integers(0, len(templates), n_req)
             with fgml.Server(streams=2, max_batch=32) as srv:
@@ -332,6 +332,33 @@ def serving_section(fgml, synth, torch, args):
 
     sweep(mixed, (0.25, 0.5, 0.75, 0.9, 1.0, 1.2), "rates")
     sweep(bf16, (0.5, 1.0, 1.5, 2.0), "bf16_only")
+    del mixed, bf16
+    # the same mixed jobs with I, alpha, F and B resident in device memory (read and
+    # written in place): latency without the host link, at multiples of the device-resident
+    # one-at-a-time capacity
+    dev_t = []
+    for i, (s, n) in enumerate(base):
+        dt = torch.float32 if i % 2 == 0 else torch.bfloat16
+        I = torch.from_numpy(s.I).to(dt).cuda()
+        A = torch.from_numpy(s.alpha).to(dt).cuda()
+        dev_t.append((I, A, n, (torch.empty_like(I), torch.empty_like(I))))
+    for I, A, _, (F, B) in dev_t:
+        fgml.estimate(I, A, None, F, B)
+    torch.cuda.synchronize()
+    calls, t0 = 0, time.perf_counter()
+    while True:
+        for I, A, n, (F, B) in dev_t:
+            fgml.estimate(I, A, None, F, B)
+            torch.cuda.synchronize()
+            calls += 1
+        dt1 = time.perf_counter() - t0
+        if dt1 >= 1.0:
+            break
+    cap_dev = calls / dt1
+    out["device_resident"] = {"one_at_a_time_req_s": cap_dev, "rates": []}
+    sweep(dev_t, (0.25, 0.5, 0.75, 1.0, 1.5), "device_rates", cap_dev)
+    out["device_resident"]["rates"] = out.pop("device_rates")
+    del dev_t
     return out
 
 
@@ -627,7 +654,11 @@ def main():
             "mixed_best_mpix_s": best(serving["rates"]),
             "bf16_best_mpix_s": best(serving["bf16_only"]),
             "p50_p99_ms_at_0.75x": next(([r["p50_ms"], r["p99_ms"]] for r in serving["rates"]
-                                          if r["x_capacity"] == 0.75), None)}
+                                          if r["x_capacity"] == 0.75), None),
+            "device_resident_p50_p99_ms_at_0.75x": next(
+                ([r["p50_ms"], r["p99_ms"]] for r in serving["device_resident"]["rates"]
+                 if r["x_capacity"] == 0.75), None),
+            "device_resident_best_mpix_s": best(serving["device_resident"]["rates"])}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
