@@ -1401,9 +1401,11 @@ void write_tune_cache(const BatchStrips &v) {
     }
 }
 
-int batch_strip_rows(int w, int h) {
+int batch_strip_rows(int w, int h, const BatchStrips *force = nullptr) {
     BatchStrips v;
-    {
+    if (force) {
+        v = *force;
+    } else {
         std::lock_guard<std::mutex> lk(g_strips_mu);
         if (!g_strips_cache_read) read_tune_cache();
         v = g_strips;
@@ -1416,7 +1418,8 @@ int batch_strip_rows(int w, int h) {
 }
 
 PassArgs batch_pass_args(const fg_params &p, const Input &in, const State &src, void *Fd,
-                         void *Bd, long long d_pitch, int w, int h) {
+                         void *Bd, long long d_pitch, int w, int h,
+                         const BatchStrips *strips = nullptr) {
     PassArgs a;
     std::memset(&a, 0, sizeof a);
     a.I = in.I;
@@ -1437,7 +1440,7 @@ PassArgs batch_pass_args(const fg_params &p, const Input &in, const State &src, 
     a.h = h;
     a.eps = p.eps_r;
     a.omega = p.omega;
-    a.strip_h = batch_strip_rows(w, h);
+    a.strip_h = batch_strip_rows(w, h, strips);
     a.n_xstrips = (w + level_pass_strip_width() - 1) / level_pass_strip_width();
     a.n_warps = a.n_xstrips * ((h + a.strip_h - 1) / a.strip_h);
     return a;
@@ -1481,7 +1484,7 @@ struct ImagePlan {
 // grid (no chunk layout); rows on the 16-byte grid always plan.
 bool plan_image(int dtype, const fg_params &p, const Input &in, const std::vector<Level> &lv, int nc,
                 void *Fd, void *Bd, long long d_pitch, void *lev0, void *lev1, size_t need,
-                ImagePlan &out) {
+                ImagePlan &out, const BatchStrips *strips = nullptr) {
     const int es = dtype == kF32 ? 4 : 2, nl = (int)lv.size();
     Buf b0{lev0, need}, b1{lev1, need};
     const Buf *bufs[2] = {&b0, &b1};
@@ -1536,7 +1539,7 @@ bool plan_image(int dtype, const fg_params &p, const Input &in, const std::vecto
             }
             BatchDesc d;
             std::memset(&d, 0, sizeof d);
-            d.a = batch_pass_args(p, in, src, F, B, dp, w, h);
+            d.a = batch_pass_args(p, in, src, F, B, dp, w, h, strips);
             d.iters = sweeps[j];
             d.dep = out.passes.empty() ? -1 : (int)out.passes.size() - 1;
             d.dep_count = out.passes.empty() ? 0 : out.passes.back().a.n_warps;
@@ -1993,6 +1996,20 @@ struct ServePlan {
     std::vector<long long> work;   // pixels x sweeps of each pass
 };
 
+// Strip shape of serving plans (FGML_SERVE_STRIPS="per_sm,lo,hi" overrides): a launch
+// often holds few jobs, so strips are short enough that each level's strips spread over
+// the SMs and the level chain of a job is not one warp walking tall strips.
+BatchStrips serve_strips() {
+    static const BatchStrips v = [] {
+        BatchStrips d{16, 4, 64};   // measured: half the single-job latency of {4, 28, 124}
+        const char *e = std::getenv("FGML_SERVE_STRIPS");
+        int a, b, c;
+        if (e && std::sscanf(e, "%d,%d,%d", &a, &b, &c) == 3 && a > 0 && b > 0 && c >= b) d = {a, b, c};
+        return d;
+    }();
+    return v;
+}
+
 size_t serve_level_bytes(int w, int h, int dtype, const fg_params &p) {
     const std::vector<Level> lv = plan_levels(w, h, p);
     return image_level_bytes(lv, coarse_levels(lv), dtype == kF32 ? 4 : 2);
@@ -2014,8 +2031,9 @@ fg_status serve_plan_create(int dtype, const fg_params &p, const void *I, long l
     const std::vector<Level> lv = plan_levels(w, h, p);
     const int nc = coarse_levels(lv);
     std::unique_ptr<ServePlan> sp(new ServePlan());
+    const BatchStrips strips = serve_strips();
     if (!plan_image(dtype, p, in, lv, nc, F, B, d_pitch, lev0, lev1, image_level_bytes(lv, nc, es),
-                    sp->image))
+                    sp->image, &strips))
         return fail(FG_ERR_CUDA, "no chunk layout for a %dx%d job", w, h);
     for (const BatchDesc &d : sp->image.passes) sp->work.push_back((long long)d.a.w * d.a.h * d.iters);
     *out = sp.release();

@@ -307,6 +307,10 @@ cudaError_t launch_level_small(int dtype, int iters, int clamp, const PassArgs &
 int level_pass_tile_rows();
 // Device error word of the library's bounded waits (0 = no error).
 cudaError_t read_and_clear_device_error(int *code, cudaStream_t s);
+// Enqueues on s copies of the two device error words into dst[0] and dst[1] (host memory,
+// pinned for the copy to stay asynchronous), without clearing them.
+cudaError_t enqueue_device_error_read(int *dst, cudaStream_t s);
+cudaError_t enqueue_tile_error_read(int *dst, cudaStream_t s);
 cudaError_t launch_coarse(int dtype, int clamp, const CoarseArgs &a, cudaStream_t s);
 // Coarse levels of many images, one block per image (list: device array of n args).
 cudaError_t launch_coarse_batch(int dtype, int clamp, const CoarseArgs *list, int n,

@@ -826,6 +826,12 @@ cudaError_t read_and_clear_device_error(int *code, cudaStream_t s) {
     return e;
 }
 
+cudaError_t enqueue_device_error_read(int *dst, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyFromSymbolAsync(dst, g_device_error, sizeof(int), 0,
+                                              cudaMemcpyDeviceToHost, s);
+    return e == cudaSuccess ? enqueue_tile_error_read(dst + 1, s) : e;
+}
+
 int level_pass_strip_width() { return kStripW; }
 int level_pass_warps_per_block() { return kWarpsPerBlock; }
 

@@ -674,6 +674,10 @@ cudaError_t read_and_clear_tile_error(int *code, cudaStream_t s) {
     return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
 }
 
+cudaError_t enqueue_tile_error_read(int *dst, cudaStream_t s) {
+    return cudaMemcpyFromSymbolAsync(dst, g_tile_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+}
+
 size_t level_tile_smem(int chunk_bytes, int slots) {
     return (size_t)kWarps * slots * (size_t)chunk_bytes + (size_t)kWarps * slots * 8;
 }

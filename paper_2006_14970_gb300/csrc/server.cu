@@ -23,7 +23,9 @@
 // another stream; it never holds a stream for its whole solve. When the launch that held
 // a job's last pass is done, its outputs are copied back (or, in device memory, complete)
 // and the job completes. Buffers and budget are released as jobs complete, and each job's
-// submit and completion times are kept for latency statistics.
+// submit and completion times are kept for latency statistics. The scheduler thread polls
+// its events without sleeping while any work is in flight (one host core), and sleeps on a
+// condition variable when idle.
 //
 // Parameter sets the work list does not run (red-black order, levels without sweeps) are
 // served whole jobs per launch through fg_estimate_batch.
@@ -71,20 +73,29 @@ constexpr size_t kWorklistReserve = 2u << 20;        // work-list bytes reserved
 constexpr size_t kPiece = 8u << 20;                  // bytes of one host copy piece at most
 constexpr size_t kPiecesInFlight = 6;                // pieces queued per direction at most
 
-// One piece of a job's host copy: `rows` rows of `width` bytes.
+// One piece of a job's copy: a contiguous copy of `bytes`, or (stage > 0) the launch that
+// copies rows onto the 16-byte grid. Host copies are always contiguous: a pitched
+// (row-by-row) copy from host memory runs at a fraction of the link's bandwidth when rows
+// are a few KB (measured: 30 GB/s at 1.2 KB rows, 100 GB/s at 6 KB, 210 GB/s contiguous).
 struct Piece {
-    void *dst;
-    const void *src;
-    size_t dpitch, spitch, width, rows;
-    cudaMemcpyKind kind;
+    void *dst = nullptr;
+    const void *src = nullptr;
+    size_t bytes = 0;
+    cudaMemcpyKind kind = cudaMemcpyHostToDevice;
+    int stage = 0;
+    fgml::StageJob jobs[2];
+    long long rows = 0;
 };
 
-void add_pieces(std::vector<Piece> &v, void *dst, size_t dpitch, const void *src, size_t spitch,
-                size_t width, size_t rows, cudaMemcpyKind kind) {
-    const size_t per = std::max<size_t>(1, kPiece / std::max<size_t>(1, width));
-    for (size_t r = 0; r < rows; r += per)
-        v.push_back(Piece{static_cast<char *>(dst) + r * dpitch, static_cast<const char *>(src) + r * spitch,
-                          dpitch, spitch, width, std::min(per, rows - r), kind});
+void add_pieces(std::vector<Piece> &v, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+    for (size_t o = 0; o < bytes; o += kPiece) {
+        Piece p;
+        p.dst = static_cast<char *>(dst) + o;
+        p.src = static_cast<const char *>(src) + o;
+        p.bytes = std::min(kPiece, bytes - o);
+        p.kind = kind;
+        v.push_back(p);
+    }
 }
 
 struct Job {
@@ -93,8 +104,10 @@ struct Job {
     size_t bytes;            // device bytes reserved for the job
     size_t level_bytes;      // each of its two intermediate-level buffers
     bool copy_in;            // I and alpha are copied into server buffers
+    bool via_raw;            // host rows off the 16-byte grid: copied up packed into dRaw first
     Clock::time_point t_submit, t_done;
     void *dI = nullptr, *dA = nullptr, *dF = nullptr, *dB = nullptr, *dL0 = nullptr, *dL1 = nullptr;
+    void *dRaw = nullptr;
     long long pI = 0, pA = 0;             // row pitches of dI and dA (elements)
     fgml::ServePlan *plan = nullptr;
     int next_pass = 0, passes = 0;        // level passes launched so far, and in all
@@ -102,6 +115,7 @@ struct Job {
     std::vector<Piece> pieces;            // the copy under way (inputs up, then outputs down)
     size_t next_piece = 0, left = 0;      // first piece not issued, bytes not issued
     bool inputs_issued = false;           // every input copy issued and inputs_ready recorded
+    cudaEvent_t allocated = nullptr;      // its buffers exist (recorded on the pool's stream)
     cudaEvent_t inputs_ready = nullptr;   // the job's inputs are on the device
     cudaEvent_t finished = nullptr;       // its outputs are back in host memory
     int state = 0;           // 0 queued, 1 in progress, 3 done, 4 failed
@@ -124,10 +138,12 @@ struct fg_server {
     bool levels = true;                  // level-granular launches (else whole jobs)
     std::vector<cudaStream_t> streams;   // compute streams
     cudaStream_t up = nullptr, down = nullptr;   // host copies, one stream per direction
+    cudaStream_t mem = nullptr;          // allocations and frees of the pool (nothing else)
     cudaMemPool_t pool = nullptr;
     size_t free_headroom = 0;            // device memory free beyond the reserve, last read
     Clock::time_point free_at{};         // when it was read
     std::vector<bool> busy;
+    int *errors = nullptr;               // pinned: the device error words after each stream's launch
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<std::shared_ptr<Job>> queue;
@@ -158,6 +174,7 @@ size_t job_bytes(const Job &j) {
     const size_t n = (size_t)r.w * r.h, es = esize(r.dtype);
     size_t b = 2 * j.level_bytes + (1u << 20);
     if (j.copy_in) b += (size_t)r.h * (round16(3LL * r.w * es) + round16((long long)r.w * es));
+    if (j.via_raw) b += n * es * 4 + 256;
     if (!(r.flags & FG_REQ_DEVICE_OUTPUT)) b += n * es * (3 + 3);
     return b;
 }
@@ -177,7 +194,7 @@ void fail_job(fg_server *s, Job &j, fg_status st, const std::string &msg) {
 // launched) and its share of the budget.
 void release(fg_server *s, Job &j) {
     const bool dout = j.req.flags & FG_REQ_DEVICE_OUTPUT;
-    cudaStream_t st = s->up;   // where every buffer was allocated
+    cudaStream_t st = s->mem;   // where every buffer was allocated
     if (j.copy_in) {
         if (j.dI) cudaFreeAsync(j.dI, st);
         if (j.dA) cudaFreeAsync(j.dA, st);
@@ -188,10 +205,12 @@ void release(fg_server *s, Job &j) {
     }
     if (j.dL0) cudaFreeAsync(j.dL0, st);
     if (j.dL1) cudaFreeAsync(j.dL1, st);
-    j.dI = j.dA = j.dF = j.dB = j.dL0 = j.dL1 = nullptr;
+    if (j.dRaw) cudaFreeAsync(j.dRaw, st);
+    j.dI = j.dA = j.dF = j.dB = j.dL0 = j.dL1 = j.dRaw = nullptr;
+    if (j.allocated) cudaEventDestroy(j.allocated);
     if (j.inputs_ready) cudaEventDestroy(j.inputs_ready);
     if (j.finished) cudaEventDestroy(j.finished);
-    j.inputs_ready = j.finished = nullptr;
+    j.allocated = j.inputs_ready = j.finished = nullptr;
     if (j.plan) fgml::serve_plan_destroy(j.plan);
     j.plan = nullptr;
     s->used -= j.bytes;
@@ -225,7 +244,7 @@ bool stage_job(fg_server *s, Job &j, std::string &why) {
     const fg_request &r = j.req;
     const int es = esize(r.dtype);
     const size_t npx = (size_t)r.w * r.h;
-    cudaStream_t up = s->up;
+    cudaStream_t up = s->mem;   // allocations go on the pool's own stream
     const bool din = r.flags & FG_REQ_DEVICE_INPUT, dout = r.flags & FG_REQ_DEVICE_OUTPUT;
     cudaError_t e = cudaSuccess;
     if (j.copy_in) {
@@ -233,6 +252,7 @@ bool stage_job(fg_server *s, Job &j, std::string &why) {
         j.pA = round16((long long)r.w * es) / es;
         e = alloc(s, &j.dI, (size_t)j.pI * es * r.h, up);
         if (e == cudaSuccess) e = alloc(s, &j.dA, (size_t)j.pA * es * r.h, up);
+        if (e == cudaSuccess && j.via_raw) e = alloc(s, &j.dRaw, npx * es * 4 + 256, up);
     } else {
         j.dI = const_cast<void *>(r.I);
         j.dA = const_cast<void *>(r.alpha);
@@ -250,8 +270,10 @@ bool stage_job(fg_server *s, Job &j, std::string &why) {
         if (e == cudaSuccess) e = alloc(s, &j.dL0, j.level_bytes, up);
         if (e == cudaSuccess) e = alloc(s, &j.dL1, j.level_bytes, up);
     }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j.allocated, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j.inputs_ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j.finished, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(j.allocated, up);
     if (e == cudaSuccess && !j.copy_in) {
         // nothing to copy: the inputs are ready once the buffers are (and the caller's event)
         e = cudaEventRecord(j.inputs_ready, up);
@@ -263,10 +285,28 @@ bool stage_job(fg_server *s, Job &j, std::string &why) {
         return false;
     }
     if (j.copy_in) {
-        const cudaMemcpyKind kind = din ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        add_pieces(j.pieces, j.dI, j.pI * es, r.I, 3LL * r.w * es, 3LL * r.w * es, r.h, kind);
-        add_pieces(j.pieces, j.dA, j.pA * es, r.alpha, (size_t)r.w * es, (size_t)r.w * es, r.h, kind);
-        j.left = (size_t)r.h * 4 * r.w * es;
+        const size_t bI = npx * 3 * es, bA = npx * es;
+        if (din || j.via_raw) {
+            // rows onto the 16-byte grid by one launch: from the caller's device buffers, or
+            // from the packed copy the host pieces put in dRaw
+            const void *sI = din ? r.I : j.dRaw;
+            const void *sA = din ? r.alpha : static_cast<char *>(j.dRaw) + ((bI + 255) & ~(size_t)255);
+            if (!din) {
+                add_pieces(j.pieces, j.dRaw, r.I, bI, cudaMemcpyHostToDevice);
+                add_pieces(j.pieces, const_cast<void *>(sA), r.alpha, bA, cudaMemcpyHostToDevice);
+            }
+            Piece p;
+            p.stage = 2;
+            p.jobs[0] = fgml::StageJob{sI, j.dI, 3LL * r.w * es, j.pI * es, 3LL * r.w * es, r.h, 0};
+            p.jobs[1] = fgml::StageJob{sA, j.dA, (long long)r.w * es, j.pA * es, (long long)r.w * es, r.h, r.h};
+            p.rows = 2LL * r.h;
+            j.pieces.push_back(p);
+        } else {
+            // host rows already on the grid: straight into place
+            add_pieces(j.pieces, j.dI, r.I, bI, cudaMemcpyHostToDevice);
+            add_pieces(j.pieces, j.dA, r.alpha, bA, cudaMemcpyHostToDevice);
+        }
+        j.left = din ? 0 : bI + bA;
     }
     if (s->levels) {
         if (fgml::serve_plan_create((int)r.dtype, s->cfg.params, j.dI, j.pI, j.dA, j.pA, j.copy_in, r.w,
@@ -319,9 +359,19 @@ void pump(fg_server *s, bool upward) {
             if ((!pick || j->left < pick->left) && (!upward || caller_ready(*j))) pick = j;
         if (!pick) break;
         Job &j = *pick;
+        if (j.next_piece == 0) cudaStreamWaitEvent(st, j.allocated, 0);   // its buffers exist
         const Piece &p = j.pieces[j.next_piece++];
-        cudaError_t e = cudaMemcpy2DAsync(p.dst, p.dpitch, p.src, p.spitch, p.width, p.rows, p.kind, st);
-        j.left -= p.width * p.rows;
+        cudaError_t e;
+        if (p.stage) {
+            fgml::StageList L;
+            std::memset(&L, 0, sizeof L);
+            L.local[0] = p.jobs[0];
+            L.local[1] = p.jobs[1];
+            e = fgml::launch_stage_rows((int)j.req.dtype, L, p.stage, p.rows, st);
+        } else {
+            e = cudaMemcpyAsync(p.dst, p.src, p.bytes, p.kind, st);
+        }
+        j.left -= p.bytes;
         if (e != cudaSuccess && j.status == FG_OK) {
             j.status = FG_ERR_CUDA;
             j.error = std::string(upward ? "copy of the inputs: " : "copy of the outputs: ") + cudaGetErrorString(e);
@@ -455,7 +505,7 @@ bool launch_step(fg_server *s) {
     }
     if (step.jobs.empty()) return false;
     cudaStream_t st = s->streams[k];
-    // complete already: orders the pool's allocations before the launch
+    // complete already: orders the pool's allocations and the copies up before the launch
     for (auto &j : step.jobs)
         if (!j->coarse_done) cudaStreamWaitEvent(st, j->inputs_ready, 0);
     fg_status status;
@@ -486,6 +536,9 @@ bool launch_step(fg_server *s) {
         s->cv_done.notify_all();
         return true;
     }
+    // the device error words as the launch leaves them, read back without a synchronisation
+    s->errors[2 * k] = s->errors[2 * k + 1] = 0;
+    fgml::enqueue_device_error_read(&s->errors[2 * k], st);
     cudaEventCreateWithFlags(&step.done, cudaEventDisableTiming);
     cudaEventRecord(step.done, st);
     for (size_t i = 0; i < step.jobs.size(); ++i) {
@@ -518,7 +571,10 @@ void retire_steps(fg_server *s) {
             dev = FG_ERR_CUDA;
             derr = cudaGetErrorString(q);
             cudaGetLastError();
-        } else if (fgml::read_and_clear_device_error(&code, s->streams[b.stream]) == cudaSuccess && code) {
+        } else if ((s->errors[2 * b.stream] || s->errors[2 * b.stream + 1]) &&
+                   fgml::read_and_clear_device_error(&code, s->streams[b.stream]) == cudaSuccess) {
+            // a launch (this one or a concurrent one) set an error word: clear it and fail
+            // this launch's jobs
             dev = FG_ERR_TIMEOUT;
             derr = "a bounded device-side wait gave up";
         }
@@ -537,10 +593,10 @@ void retire_steps(fg_server *s) {
                 s->finishing.push_back(jp);   // `finished` was never recorded: complete
                 continue;
             }
-            const size_t row = (size_t)j.req.w * 3 * esize(j.req.dtype);
-            add_pieces(j.pieces, j.req.F, row, j.dF, row, row, j.req.h, cudaMemcpyDeviceToHost);
-            add_pieces(j.pieces, j.req.B, row, j.dB, row, row, j.req.h, cudaMemcpyDeviceToHost);
-            j.left = 2 * row * j.req.h;
+            const size_t bytes = (size_t)j.req.w * j.req.h * 3 * esize(j.req.dtype);
+            add_pieces(j.pieces, j.req.F, j.dF, bytes, cudaMemcpyDeviceToHost);
+            add_pieces(j.pieces, j.req.B, j.dB, bytes, cudaMemcpyDeviceToHost);
+            j.left = 2 * bytes;
             s->downloading.push_back(jp);
         }
         cudaEventDestroy(b.done);
@@ -611,8 +667,15 @@ void worker_main(fg_server *s) {
         const bool active = !s->running.empty() || !s->finishing.empty() || !s->admitted.empty() ||
                             !s->downloading.empty() || !s->up_pieces.empty() || !s->down_pieces.empty();
         if (s->stop && s->queue.empty() && !active) break;
-        // nothing to launch: sleep until a submission or a short poll interval passes
-        s->cv_work.wait_for(lk, std::chrono::microseconds(active ? 20 : 2000));
+        if (active) {
+            // work in flight: poll its events again at once, letting submitters in
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
+        } else {
+            // idle: sleep until a submission (or a long poll interval)
+            s->cv_work.wait_for(lk, std::chrono::microseconds(2000));
+        }
     }
 }
 
@@ -626,7 +689,7 @@ void destroy_streams(fg_server *s) {
         fg_release_workspace(x);
         cudaStreamDestroy(x);
     }
-    for (cudaStream_t *x : {&s->up, &s->down})
+    for (cudaStream_t *x : {&s->up, &s->down, &s->mem})
         if (*x) {
             cudaStreamSynchronize(*x);
             cudaStreamDestroy(*x);
@@ -641,6 +704,8 @@ void destroy_streams(fg_server *s) {
     s->streams.clear();
     if (s->pool) cudaMemPoolDestroy(s->pool);
     s->pool = nullptr;
+    if (s->errors) cudaFreeHost(s->errors);
+    s->errors = nullptr;
 }
 
 }  // namespace
@@ -692,7 +757,8 @@ fg_status fg_server_create(const fg_server_cfg *cfg, fg_server **out) {
     }
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    bool ok = true;
+    bool ok = cudaMallocHost((void **)&s->errors, 2 * sizeof(int) * c.streams) == cudaSuccess;
+    if (ok) std::memset(s->errors, 0, 2 * sizeof(int) * c.streams);
     for (int i = 0; i < c.streams && ok; ++i) {
         cudaStream_t a = nullptr;
         ok = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) == cudaSuccess;
@@ -701,11 +767,24 @@ fg_status fg_server_create(const fg_server_cfg *cfg, fg_server **out) {
         if (ok && s->levels) ok = fgml::serve_reserve(a, kWorklistReserve) == FG_OK;
     }
     ok = ok && cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking) == cudaSuccess &&
-         cudaStreamCreateWithFlags(&s->down, cudaStreamNonBlocking) == cudaSuccess;
+         cudaStreamCreateWithFlags(&s->down, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&s->mem, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         destroy_streams(s.get());
         return sfail(FG_ERR_CUDA, "stream or workspace creation failed");
+    }
+    // the pool takes its first memory now (a quarter of the budget, at most 8 GiB, returned
+    // to the pool at once and kept there), so that the first jobs do not wait for the
+    // driver to map pages
+    {
+        const size_t warm = std::min<size_t>((size_t)c.hbm_budget_bytes / 4, 8ull << 30);
+        void *p = nullptr;
+        if (warm && cudaMallocFromPoolAsync(&p, warm, s->pool, s->mem) == cudaSuccess) {
+            cudaFreeAsync(p, s->mem);
+            cudaStreamSynchronize(s->mem);
+        }
+        cudaGetLastError();
     }
     fg_server *raw = s.release();
     raw->worker = std::thread(worker_main, raw);
@@ -733,6 +812,7 @@ fg_status fg_server_submit(fg_server *s, const fg_request *r, uint64_t *ticket) 
     j->level_bytes = s->levels ? fgml::serve_level_bytes(r->w, r->h, (int)r->dtype, s->cfg.params) : 0;
     j->copy_in = !(r->flags & FG_REQ_DEVICE_INPUT) ||
                  !(on_grid(r->I, 3LL * r->w * es) && on_grid(r->alpha, (long long)r->w * es));
+    j->via_raw = !(r->flags & FG_REQ_DEVICE_INPUT) && ((long long)r->w * es) % 16 != 0;
     j->bytes = job_bytes(*j);
     if ((long long)j->bytes > s->cfg.hbm_budget_bytes)
         return sfail(FG_ERR_INVALID_ARG, "job needs %zu device bytes, above the budget of %lld",
