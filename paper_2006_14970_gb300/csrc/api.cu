@@ -921,9 +921,11 @@ fg_status fg_estimate_composite(const fg_image *I, const fg_image *alpha, const 
 
 namespace {
 
-// Host buffers in, host buffers out, on `s`: copies of I and alpha into the stream's
-// staging buffers (rows padded to 16 bytes, so the level passes can take the tile path
-// without another copy), the solve, copies of F and B back; `sync` waits for the stream.
+// Host buffers in, host buffers out, on `s`: contiguous copies of I and alpha into the
+// stream's staging buffers (a pitched copy from host memory runs at a fraction of the
+// link's bandwidth when rows are a few KB), the solve (which first puts rows that are off
+// the 16-byte grid onto it, on the device), contiguous copies of F and B back; `sync`
+// waits for the stream.
 fg_status estimate_host(const void *I, const void *alpha, int w, int h, fg_dtype dtype,
                         const fg_params *params, void *F, void *B, cudaStream_t s, bool sync) {
     g_err.clear();
@@ -938,19 +940,16 @@ fg_status estimate_host(const void *I, const void *alpha, int w, int h, fg_dtype
     if (st != FG_OK) return st;
     const int es = elem_size(dtype);
     const size_t n = (size_t)w * h;
-    const size_t rowI = 3ull * w * es, rowA = (size_t)w * es;
-    const size_t pI = (rowI + 15) & ~(size_t)15, pA = (rowA + 15) & ~(size_t)15;
-    const size_t bI = align256(pI * h), bA = align256(pA * h), bO = align256(3 * n * es);
+    const size_t bI = align256(3 * n * es), bA = align256(n * es), bO = bI;
     Workspace &ws = workspace_for(s);
     if ((st = ensure(ws.stage, bI + bA + 2 * bO, s)) != FG_OK) return st;
     char *dI = (char *)ws.stage.p, *dA = dI + bI, *dF = dA + bA, *dB = dF + bO;
     cudaError_t e;
-    if ((e = cudaMemcpy2DAsync(dI, pI, I, rowI, rowI, h, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(dI, I, 3 * n * es, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "copy of I to the device");
-    if ((e = cudaMemcpy2DAsync(dA, pA, alpha, rowA, rowA, h, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(dA, alpha, n * es, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "copy of alpha to the device");
-    // the staging rows are padded to 16 bytes and readable up to their pitch
-    Input in{dI, dA, (long long)(pI / es), (long long)(pA / es), w, h, true};
+    Input in{dI, dA, 3LL * w, (long long)w, w, h, false};
     if ((st = estimate(in, (int)dtype, p, dF, dB, 3LL * w, s)) != FG_OK) return st;
     if ((e = cudaMemcpyAsync(F, dF, 3 * n * es, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(e, "copy of F to the host");

@@ -774,11 +774,11 @@ fg_status fg_server_create(const fg_server_cfg *cfg, fg_server **out) {
         destroy_streams(s.get());
         return sfail(FG_ERR_CUDA, "stream or workspace creation failed");
     }
-    // the pool takes its first memory now (a quarter of the budget, at most 8 GiB, returned
-    // to the pool at once and kept there), so that the first jobs do not wait for the
-    // driver to map pages
+    // the pool takes its memory now (half the budget, at most 32 GiB, returned to the pool
+    // at once and kept there), so that jobs do not wait for the driver to map pages when
+    // a burst raises the memory in use
     {
-        const size_t warm = std::min<size_t>((size_t)c.hbm_budget_bytes / 4, 8ull << 30);
+        const size_t warm = std::min<size_t>((size_t)c.hbm_budget_bytes / 2, 32ull << 30);
         void *p = nullptr;
         if (warm && cudaMallocFromPoolAsync(&p, warm, s->pool, s->mem) == cudaSuccess) {
             cudaFreeAsync(p, s->mem);
