@@ -302,6 +302,15 @@ int strip_rows(int w, int h, int blocks_per_sm = 2) {
     return (int)std::max<long long>(r, 1);
 }
 
+// FGML_CONE=0 runs the small levels of a solve one launch each (for comparison).
+bool cone_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("FGML_CONE");
+        return !(e && *e == '0');
+    }();
+    return on;
+}
+
 // Levels up to this many pixels run in the small-level kernel (latency bound);
 // FGML_SMALL_LEVEL_PIXELS overrides it for tuning.
 long long small_level_pixels() {
@@ -584,6 +593,60 @@ bool needs_stage(const Input &in, int es) {
     return es == 2 && !(words(in.I, in.I_pitch * es) && words(in.A, in.A_pitch * es));
 }
 
+// Last level of the run of small levels above the coarse ones that one cone launch
+// computes: consecutive levels of at most small_level_pixels() each (at most
+// kConeMaxLevels of them), Jacobi order only; nc - 1 when there is none.
+int cone_run(const std::vector<Level> &lv, int nc, const fg_params &p) {
+    int m = nc - 1;
+    if (p.order != FG_ORDER_JACOBI || nc < 1 || !cone_enabled()) return m;
+    while (m + 1 < (int)lv.size() && m + 1 - nc < kConeMaxLevels &&
+           (long long)lv[m + 1].w * lv[m + 1].h <= small_level_pixels())
+        ++m;
+    return m;
+}
+
+// Arguments of the cone launch for levels nc..m, reading the coarse kernel's output
+// `src`; false when the largest region of a block would need more than kConeSmemMax bytes
+// of shared memory (many sweeps per level), and the levels then run one launch each.
+constexpr size_t kConeSmemMax = 100 * 1024;
+bool plan_cone(const Input &in, const std::vector<Level> &lv, int nc, int m, const State &src,
+               const fg_params &p, ConeArgs &a) {
+    std::memset(&a, 0, sizeof a);
+    a.I = in.I;
+    a.I_pitch = in.I_pitch;
+    a.A = in.A;
+    a.A_pitch = in.A_pitch;
+    a.Iw = in.w;
+    a.Ih = in.h;
+    a.Fs = src.F;
+    a.Bs = src.B;
+    a.s_pitch = src.pitch;
+    a.sw = src.w;
+    a.sh = src.h;
+    a.eps = p.eps_r;
+    a.omega = p.omega;
+    a.nlev = m - nc + 1;
+    for (int i = 0; i < a.nlev; ++i) {
+        a.lw[i] = lv[nc + i].w;
+        a.lh[i] = lv[nc + i].h;
+        a.lk[i] = lv[nc + i].k;
+    }
+    // the largest region over the blocks (edge blocks are clipped, interior ones alike)
+    const int gx = (a.lw[a.nlev - 1] + kConeTW - 1) / kConeTW, gy = (a.lh[a.nlev - 1] + kConeTH - 1) / kConeTH;
+    long long cap = 0;
+    ConeRect E[kConeMaxLevels], Rc;
+    auto cells = [](const ConeRect &r) { return (long long)(r.x1 - r.x0 + 1) * (r.y1 - r.y0 + 1); };
+    for (int by = 0; by < gy; ++by)
+        for (int bx = 0; bx < gx; ++bx) {
+            cone_regions(a, bx, by, E, &Rc);
+            cap = std::max(cap, cells(Rc));
+            for (int i = 0; i < a.nlev; ++i) cap = std::max(cap, cells(E[i]));
+        }
+    if (cone_smem_bytes((int)std::min<long long>(cap, 1 << 24)) > kConeSmemMax) return false;
+    a.cap = (int)cap;
+    return true;
+}
+
 // The kernels of one solve, enqueued on `s` (no allocation, no synchronisation).
 fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
                           const std::vector<Level> &lv, int nc, void *Fd, void *Bd,
@@ -644,7 +707,36 @@ fg_status launch_sequence(const Input &in, int dtype, const fg_params &p,
     cudaError_t e = launch_coarse(dtype, p.clamp, ca, s);
     if (e != cudaSuccess) return cuda_fail(e, "coarse kernel launch");
 
-    for (int l = nc; l < n; ++l) {
+    int l = nc;
+    // the run of small levels after the coarse ones, in one launch (Jacobi order)
+    ConeArgs cone;
+    const int m = cone_run(lv, nc, p);
+    if (m >= nc && plan_cone(in, lv, nc, m, src, p, cone)) {
+        State dst{};
+        int nb = buf;
+        if (m == n - 1) {
+            cone.Fd = Fd;
+            cone.Bd = Bd;
+            cone.d_pitch = d_pitch;
+            if (cmp) {
+                cone.Bn = cmp->Bn;
+                cone.In = cmp->In;
+                cone.bn_pitch = cmp->bn_pitch;
+                cone.in_pitch = cmp->in_pitch;
+            }
+        } else {
+            nb = buf == 0 ? 1 : 0;
+            dst = state_in(ws.lev[nb], lv[m].w, lv[m].h, es);
+            cone.Fd = (void *)dst.F;
+            cone.Bd = (void *)dst.B;
+            cone.d_pitch = dst.pitch;
+        }
+        if ((e = launch_cone(dtype, p.clamp, cone, s)) != cudaSuccess) return cuda_fail(e, "small-level launch");
+        src = dst;
+        buf = nb;
+        l = m + 1;
+    }
+    for (; l < n; ++l) {
         fg_status st = run_level(dtype, p, in, src, buf, lv[l].k, lv[l].w, lv[l].h, l == n - 1,
                                  Fd, Bd, d_pitch, ws, es, s, l == n - 1 ? cmp : nullptr);
         if (st != FG_OK) return st;

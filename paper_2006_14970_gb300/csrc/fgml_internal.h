@@ -302,6 +302,63 @@ cudaError_t read_and_clear_tile_error(int *code, cudaStream_t s);
 // Small-level variant: one block per 32 x 16 output tile, all sweeps in shared memory.
 // Red-black order: `iters` (1 or 2) red-black iterations of a level in one launch.
 cudaError_t launch_level_rb(int dtype, int iters, int clamp, const PassArgs &a, cudaStream_t s);
+// ---- cone kernel (cone.cu): a run of small levels in one launch.
+// Each block owns a 32 x 16 tile of the run's last level and computes, in shared memory,
+// every level of the run on the region its tile depends on (its dependency cone): the
+// region a level's sweeps need, expanded by that level's sweep count, mapped down to the
+// level below by the nearest-resize rule, back to the state the coarse kernel left.
+constexpr int kConeMaxLevels = 8;
+constexpr int kConeTW = 32, kConeTH = 16;
+
+struct ConeRect {
+    int x0, y0, x1, y1;   // inclusive
+};
+
+struct ConeArgs {
+    const void *I;
+    long long I_pitch;
+    const void *A;
+    long long A_pitch;
+    int Iw, Ih;
+    const void *Fs, *Bs;       // state of the level below the run (pitch s_pitch elements)
+    long long s_pitch;
+    int sw, sh;
+    void *Fd, *Bd;             // state of the run's last level
+    long long d_pitch;
+    float eps, omega;
+    int nlev;
+    int lw[kConeMaxLevels], lh[kConeMaxLevels], lk[kConeMaxLevels];
+    int cap;                   // cells of the largest region of any block (shared-memory sizing)
+    const void *Bn;            // compositing epilogue (run ending at the top level), as PassArgs
+    void *In;
+    long long bn_pitch, in_pitch;
+};
+
+// The regions of block (bx, by): E[l] = the cells of level l its sweeps start from, and
+// *Rc = the cells of the level below the run that the first level's start reads.
+__host__ __device__ inline int cone_lo(int a, int b) { return a < b ? a : b; }
+__host__ __device__ inline int cone_hi(int a, int b) { return a > b ? a : b; }
+
+__host__ __device__ inline void cone_regions(const ConeArgs &a, int bx, int by, ConeRect *E,
+                                             ConeRect *Rc) {
+    const int L = a.nlev - 1;
+    ConeRect R{bx * kConeTW, by * kConeTH, cone_lo(bx * kConeTW + kConeTW - 1, a.lw[L] - 1),
+               cone_lo(by * kConeTH + kConeTH - 1, a.lh[L] - 1)};
+    for (int l = L; l >= 0; --l) {
+        const int w = a.lw[l], h = a.lh[l], k = a.lk[l];
+        const ConeRect e{cone_hi(R.x0 - k, 0), cone_hi(R.y0 - k, 0), cone_lo(R.x1 + k, w - 1),
+                         cone_lo(R.y1 + k, h - 1)};
+        E[l] = e;
+        const int pw = l > 0 ? a.lw[l - 1] : a.sw, ph = l > 0 ? a.lh[l - 1] : a.sh;
+        R = ConeRect{nearest_src(e.x0, pw, w), nearest_src(e.y0, ph, h), nearest_src(e.x1, pw, w),
+                     nearest_src(e.y1, ph, h)};
+    }
+    *Rc = R;
+}
+
+cudaError_t launch_cone(int dtype, int clamp, const ConeArgs &a, cudaStream_t s);
+size_t cone_smem_bytes(int cap);
+
 cudaError_t launch_level_small(int dtype, int iters, int clamp, const PassArgs &a,
                                cudaStream_t s);
 int level_pass_tile_rows();
