@@ -528,9 +528,14 @@ def main():
 
     s, w, h, I, A, F, B = image_case(WORKLOAD)
     levels = fgml.schedule(w, h)
-    # one launch for the levels of at most 1024 pixels, one per level pass after them
+    # one launch for the levels of at most 1024 pixels (the coarse kernel), one for the run
+    # of levels of at most 0.3 Mpx after them (the cone kernel), one per level pass above
     n_coarse = sum(1 for (lw, lh, _) in levels if lw * lh <= 1024)
-    launches_per_step = 1 + (len(levels) - n_coarse)
+    n_cone = 0
+    while (n_coarse + n_cone < len(levels) and n_cone < 8
+           and levels[n_coarse + n_cone][0] * levels[n_coarse + n_cone][1] <= 300000):
+        n_cone += 1
+    launches_per_step = 1 + int(n_cone > 0) + (len(levels) - n_coarse - n_cone)
 
     with Clocks(local) as clk:
         ms = timed(lambda: fgml.estimate(I, A, None, F, B), args.steps, args.warmup)
