@@ -69,7 +69,8 @@ struct Lane {
     int oI0, oI1, oA0, oA1, oS0, oS1;   // byte offsets of the two pixels in a row of the slot
     bool pairs;          // 16-bit, I and alpha by gather of an identity level: p1 follows p0
     bool o0, o1;         // the lane writes p0 / p1
-    bool vst;            // paired stores allowed (o0 && o1 and aligned)
+    bool vst;            // paired stores allowed (o0 && o1, outputs' bases aligned for pairs)
+    bool odd;            // the output pitch is half a pair off: odd rows start mid-pair
     long long col;       // byte offset of p0 in an output row
 };
 
@@ -161,7 +162,17 @@ __device__ __forceinline__ void store_row(const PassArgs &p, const Lane &L, int 
     const long long pitch = p.d_pitch * (long long)sizeof(T);
     T *Fr = reinterpret_cast<T *>(static_cast<unsigned char *>(p.Fd) + (long long)y * pitch + L.col);
     T *Br = reinterpret_cast<T *>(static_cast<unsigned char *>(p.Bd) + (long long)y * pitch + L.col);
-    if (L.vst) {
+    if (L.vst && L.odd && (y & 1)) {
+        // the row starts half a pair off the pair grid: pairs from the second element on
+        st_elem(Fr + 0, v.F[0].x);
+        st_pair(Fr + 1, v.F[1].x, v.F[2].x);
+        st_pair(Fr + 3, v.F[0].y, v.F[1].y);
+        st_elem(Fr + 5, v.F[2].y);
+        st_elem(Br + 0, v.B[0].x);
+        st_pair(Br + 1, v.B[1].x, v.B[2].x);
+        st_pair(Br + 3, v.B[0].y, v.B[1].y);
+        st_elem(Br + 5, v.B[2].y);
+    } else if (L.vst) {
         st_pair(Fr + 0, v.F[0].x, v.F[1].x);
         st_pair(Fr + 2, v.F[2].x, v.F[0].y);
         st_pair(Fr + 4, v.F[1].y, v.F[2].y);
@@ -335,8 +346,9 @@ __device__ __forceinline__ bool tile_strip(const PassArgs &p, const CUtensorMap 
         L.o1 = mid && x + 1 < p.w;
         L.col = 3LL * max(x, 0) * es;
         const int al = es == 4 ? 7 : 3;
-        L.vst = L.o0 && L.o1 && ((reinterpret_cast<uintptr_t>(p.Fd) | reinterpret_cast<uintptr_t>(p.Bd)) & al) == 0 &&
-                ((p.d_pitch * es) & al) == 0;
+        // pitches are whole elements, so a pitch off the pair grid is off by exactly one element
+        L.vst = L.o0 && L.o1 && ((reinterpret_cast<uintptr_t>(p.Fd) | reinterpret_cast<uintptr_t>(p.Bd)) & al) == 0;
+        L.odd = ((p.d_pitch * es) & al) != 0;
     }
     // lanes 0..3 issue the gathers of I, alpha, F and B: their map, box x and offset
     const CUtensorMap *map = lane == 0 ? mI : lane == 1 ? mA : lane == 2 ? mF : mB;
