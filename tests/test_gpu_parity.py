@@ -291,3 +291,37 @@ def test_outputs_leave_guard_bands_untouched(fgml):
         assert bool((b[~inner] == sentinel).all())
     Fo, Bo = oracle.ml(s.I, s.alpha)
     assert np.abs(F.cpu().numpy() - Fo).max() <= 1e-4
+
+
+_ONE_SOLVE = """
+import sys
+import numpy as np, torch
+from paper_2006_14970_gb300 import fgml, synth
+w, h, dt = int(sys.argv[2]), int(sys.argv[3]), getattr(torch, sys.argv[4])
+s = synth.make_sample(w, h, 4242)
+F, B = fgml.estimate(torch.from_numpy(s.I).cuda().to(dt), torch.from_numpy(s.alpha).cuda().to(dt))
+np.save(sys.argv[1], torch.cat([F, B], 2).float().cpu().numpy())
+"""
+
+
+@pytest.mark.parametrize("w,h,dt", [(1024, 768, "float32"), (2047, 1535, "float32"),
+                                    (700, 1100, "bfloat16")])
+def test_small_levels_in_one_launch_match_one_launch_per_level(fgml, tmp_path, w, h, dt):
+    # the run of small levels above the coarse ones as one launch (each block computing its
+    # tile's dependency cone) against one launch per level (FGML_CONE=0, read once per
+    # process, hence the separate processes): the same sweeps on the same values, so the
+    # results agree to float32 rounding of the sums (16-bit: both round each level to the
+    # storage type)
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for cone in ("1", "0"):
+        path = str(tmp_path / f"out_{cone}.npy")
+        env = dict(os.environ, FGML_CONE=cone, PYTHONPATH=root)
+        subprocess.run([sys.executable, "-c", _ONE_SOLVE, path, str(w), str(h), dt], cwd=root,
+                       env=env, check=True, timeout=600)
+        outs.append(np.load(path))
+    tol = 1e-5 if dt == "float32" else 2 ** -6
+    assert np.abs(outs[0] - outs[1]).max() <= tol
