@@ -637,17 +637,25 @@ bool plan_cone(const Input &in, const std::vector<Level> &lv, int nc, int m, con
     }
     // the largest region over the blocks (edge blocks are clipped, interior ones alike)
     const int gx = (a.lw[a.nlev - 1] + kConeTW - 1) / kConeTW, gy = (a.lh[a.nlev - 1] + kConeTH - 1) / kConeTH;
-    long long cap = 0;
+    long long cap = 0, io = 0;
     ConeRect E[kConeMaxLevels], Rc;
     auto cells = [](const ConeRect &r) { return (long long)(r.x1 - r.x0 + 1) * (r.y1 - r.y0 + 1); };
     for (int by = 0; by < gy; ++by)
         for (int bx = 0; bx < gx; ++bx) {
             cone_regions(a, bx, by, E, &Rc);
             cap = std::max(cap, cells(Rc));
-            for (int i = 0; i < a.nlev; ++i) cap = std::max(cap, cells(E[i]));
+            long long sum = 0;
+            for (int i = 0; i < a.nlev; ++i) {
+                cap = std::max(cap, cells(E[i]));
+                sum += cells(E[i]);
+            }
+            io = std::max(io, sum);
         }
-    if (cone_smem_bytes((int)std::min<long long>(cap, 1 << 24)) > kConeSmemMax) return false;
+    if (cone_smem_bytes((int)std::min<long long>(cap, 1 << 20), (int)std::min<long long>(io, 1 << 20)) >
+        kConeSmemMax)
+        return false;
     a.cap = (int)cap;
+    a.io = (int)io;
     return true;
 }
 

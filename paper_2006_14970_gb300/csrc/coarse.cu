@@ -33,8 +33,10 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs &p);
 template <typename T, bool CLAMP>
 __global__ void __launch_bounds__(kThreads, 1) coarse_kernel(const CoarseArgs p) {
     pdl_enter();
-    coarse_body<T, CLAMP>(p);
+    // release the next launch at once: its blocks fetch their inputs while this single
+    // block runs (they wait for this kernel before reading what it writes)
     pdl_leave();
+    coarse_body<T, CLAMP>(p);
 }
 
 // One block per image of a batch; each reads its arguments from the device list.

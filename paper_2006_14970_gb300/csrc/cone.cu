@@ -40,16 +40,44 @@ __global__ void __launch_bounds__(kThreads) cone_kernel(const ConeArgs a) {
     __shared__ ConeRect E[kConeMaxLevels];
     __shared__ ConeRect Rc;
     const int cap = a.cap;
-    // two state buffers (6 channels each: F then B), alpha, I (3 channels); a level's
-    // cells are indexed in the frame of its region E[l], row-major
+    __shared__ int off[kConeMaxLevels];   // first cell of each level in the alpha/I area
+    // two state buffers (6 channels each: F then B), then per level alpha and I (3
+    // channels) of its region; a level's cells are indexed in the frame of its region E[l],
+    // row-major
     float *P = sm, *Q = sm + 6 * cap;
-    float *sAl = sm + 12 * cap, *sIm = sm + 13 * cap;
-    pdl_enter();
+    float *const io = sm + 12 * cap;
     const int tid = threadIdx.x;
-    if (tid == 0) cone_regions(a, blockIdx.x, blockIdx.y, E, &Rc);
+    if (tid == 0) {
+        cone_regions(a, blockIdx.x, blockIdx.y, E, &Rc);
+        int o = 0;
+        for (int l = 0; l < a.nlev; ++l) {
+            off[l] = o;
+            o += 4 * (E[l].x1 - E[l].x0 + 1) * (E[l].y1 - E[l].y0 + 1);
+        }
+    }
     __syncthreads();
     const T *I = static_cast<const T *>(a.I);
     const T *A = static_cast<const T *>(a.A);
+
+    // alpha and I of every level's region, requested before the wait for the coarse
+    // kernel: they are the solve's inputs, complete before the coarse kernel (which
+    // writes only the state read below) was let through its own wait and released this
+    // launch
+    for (int l = 0; l < a.nlev; ++l) {
+        const ConeRect e = E[l];
+        const int w = a.lw[l], h = a.lh[l];
+        const int ew = e.x1 - e.x0 + 1, n = ew * (e.y1 - e.y0 + 1);
+        float *al = io + off[l], *im = al + n;
+        for (int i = tid; i < n; i += kThreads) {
+            const int xx = i % ew, yy = i / ew;
+            const int gx = nearest_src(e.x0 + xx, a.Iw, w), gy = nearest_src(e.y0 + yy, a.Ih, h);
+            al[i] = ld_elem(A + (long long)gy * a.A_pitch + gx);
+            const T *Ip = I + (long long)gy * a.I_pitch + 3 * gx;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) im[c * n + i] = ld_elem(Ip + c);
+        }
+    }
+    pdl_enter();
 
     // the region of the level below the run, as the coarse kernel left it
     ConeRect pf = Rc;
@@ -75,17 +103,13 @@ __global__ void __launch_bounds__(kThreads) cone_kernel(const ConeArgs a) {
         const ConeRect e = E[l];
         const int ew = e.x1 - e.x0 + 1, n = ew * (e.y1 - e.y0 + 1);
         const int pfw = pf.x1 - pf.x0 + 1;
-        __syncthreads();   // P complete; nothing reads Q, alpha or I of the level below any more
+        const float *sAl = io + off[l], *sIm = sAl + n;
+        __syncthreads();   // P complete; nothing reads Q any more
         for (int i = tid; i < n; i += kThreads) {
             const int x = e.x0 + i % ew, y = e.y0 + i / ew;
             const int j = (nearest_src(y, phl, h) - pf.y0) * pfw + (nearest_src(x, pwl, w) - pf.x0);
 #pragma unroll
             for (int c = 0; c < 6; ++c) Q[c * cap + i] = round_to<T>(P[c * cap + j]);
-            const int gx = nearest_src(x, a.Iw, w), gy = nearest_src(y, a.Ih, h);
-            sAl[i] = ld_elem(A + (long long)gy * a.A_pitch + gx);
-            const T *Ip = I + (long long)gy * a.I_pitch + 3 * gx;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sIm[c * cap + i] = ld_elem(Ip + c);
         }
         {
             float *t = P;
@@ -121,7 +145,7 @@ __global__ void __launch_bounds__(kThreads) cone_kernel(const ConeArgs a) {
                 const float m = __fdividef(1.f, fmaf(A00, A11, -A01 * A01));
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float Ic = sIm[c * cap + c0];
+                    const float Ic = sIm[c * n + c0];
                     const float bF = fmaf(ai, Ic, sF[c]), bB = fmaf(be, Ic, sB[c]);
                     float gF = (A11 * bF - A01 * bB) * m;
                     float gB = (A00 * bB - A01 * bF) * m;
@@ -163,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) cone_kernel(const ConeArgs a) {
             st_elem(Fp + c, v[c]);
             st_elem(Bp + c, v[3 + c]);
         }
-        if (a.In) composite_px<T>(a.Bn, a.bn_pitch, a.In, a.in_pitch, x, y, sAl[c0], v);
+        if (a.In) composite_px<T>(a.Bn, a.bn_pitch, a.In, a.in_pitch, x, y, io[off[L] + c0], v);
     }
     pdl_leave();
 }
@@ -172,7 +196,7 @@ template <typename T, bool CLAMP>
 cudaError_t launch_t(const ConeArgs &a, cudaStream_t s) {
     const int L = a.nlev - 1;
     const dim3 grid((a.lw[L] + kConeTW - 1) / kConeTW, (a.lh[L] + kConeTH - 1) / kConeTH);
-    const size_t smem = cone_smem_bytes(a.cap);
+    const size_t smem = cone_smem_bytes(a.cap, a.io);
     cudaError_t e = allow_dynamic_smem(cone_kernel<T, CLAMP>);
     if (e != cudaSuccess) return e;
     return launch_pdl(cone_kernel<T, CLAMP>, grid, dim3(kThreads), smem, s, a);
@@ -180,10 +204,10 @@ cudaError_t launch_t(const ConeArgs &a, cudaStream_t s) {
 
 }  // namespace
 
-size_t cone_smem_bytes(int cap) { return (size_t)cap * 16 * sizeof(float); }
+size_t cone_smem_bytes(int cap, int io) { return ((size_t)cap * 12 + (size_t)io * 4) * sizeof(float); }
 
 cudaError_t launch_cone(int dtype, int clamp, const ConeArgs &a, cudaStream_t s) {
-    if (a.nlev < 1 || a.nlev > kConeMaxLevels || a.cap < 1) return cudaErrorInvalidValue;
+    if (a.nlev < 1 || a.nlev > kConeMaxLevels || a.cap < 1 || a.io < 1) return cudaErrorInvalidValue;
     if ((a.lh[a.nlev - 1] + kConeTH - 1) / kConeTH > 65535) return cudaErrorInvalidValue;
     switch (dtype) {
         case kF32: return clamp ? launch_t<float, true>(a, s) : launch_t<float, false>(a, s);

@@ -329,6 +329,7 @@ struct ConeArgs {
     int nlev;
     int lw[kConeMaxLevels], lh[kConeMaxLevels], lk[kConeMaxLevels];
     int cap;                   // cells of the largest region of any block (shared-memory sizing)
+    int io;                    // cells of all the run's regions of a block together, at most
     const void *Bn;            // compositing epilogue (run ending at the top level), as PassArgs
     void *In;
     long long bn_pitch, in_pitch;
@@ -357,7 +358,7 @@ __host__ __device__ inline void cone_regions(const ConeArgs &a, int bx, int by, 
 }
 
 cudaError_t launch_cone(int dtype, int clamp, const ConeArgs &a, cudaStream_t s);
-size_t cone_smem_bytes(int cap);
+size_t cone_smem_bytes(int cap, int io);
 
 cudaError_t launch_level_small(int dtype, int iters, int clamp, const PassArgs &a,
                                cudaStream_t s);
