@@ -9,11 +9,13 @@
 // level's borders, where the clamped neighbour is the cell itself); that start state is
 // the nearest resize of the level below (Algorithm 1), so it depends on the source range
 // of the expanded region there, and so on down to the level the coarse kernel wrote. The
-// block loads that bottom region, then for each level: resizes the level below into the
-// expanded region, gathers I and alpha there (nearest resize of the full-resolution input),
-// and runs the sweeps on a region that shrinks by one cell per sweep on every side not at
-// the level's border (the cells whose neighbours are all still exact), ending on a region
-// that covers what the next level reads. Between levels the state is rounded to the
+// block first gathers I and alpha of every level's region (nearest resize of the
+// full-resolution input) — before it waits for the coarse kernel, which releases this
+// launch as it starts, so the gathers overlap the coarse levels — then loads the bottom
+// region of the state, and for each level resizes the level below into the expanded
+// region and runs the sweeps on a region that shrinks by one cell per sweep on every side
+// not at the level's border (the cells whose neighbours are all still exact), ending on a
+// region that covers what the next level reads. Between levels the state is rounded to the
 // storage type, as the per-level kernels store it. The per-pixel solve is the closed form
 // of Section III-C with the same operation order as the small-level kernel, clamped to
 // [0, 1]. Neighbouring blocks recompute the overlap of their regions; at the lower levels
