@@ -217,7 +217,7 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs &p) {
                     // Jacobi: every pixel from the previous values; red-black: one colour
                     // per round, the other keeps its value
                     // every lane of the warp computes (the shuffles need them all), then
-                    // keeps the solution only where its pixel is updated this round
+                    // keeps the solution only where its pixel is updated in this half-sweep
                     float2 nv[2];
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
