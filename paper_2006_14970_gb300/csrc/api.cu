@@ -46,7 +46,6 @@ fg_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 constexpr int kMaxSide = 32767;
-constexpr int kMaxLevels = 32;
 
 int elem_size(fg_dtype d) { return d == FG_F32 ? 4 : 2; }
 
