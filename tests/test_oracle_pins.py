@@ -295,6 +295,27 @@ def test_alpha_one_gives_zero_background_and_foreground_equal_constant_image():
     assert np.max(np.abs(B - 0.37)) < 1e-12
 
 
+@pytest.mark.parametrize("order", [JACOBI, REDBLACK, RASTER_GS])
+def test_alpha_one_keeps_the_foreground_within_the_smoothing_bound_of_the_image(order):
+    # alpha = 1 on a non-constant image: U = (1, 0) and every edge weight is eps_r
+    # (omega |d alpha| = 0), so the 2x2 system is diagonal and each update sets
+    # (1 + 4 eps_r) F_i = I_i + eps_r * sum_j F_j (a clamped neighbour being F_i itself).
+    # Hence F_i - I_i = eps_r * sum_j (F_j - I_i) / (1 + 4 eps_r), at most
+    # 4 eps_r / (1 + 4 eps_r) in size with F and I in [0, 1], after any number of sweeps
+    # from any start. B only averages its neighbours and keeps its initial 0. Mirrored
+    # for alpha = 0.
+    I, _ = _inputs(31, 43, 11)
+    p = Params(order=order)
+    bound = 4 * p.eps_r / (1 + 4 * p.eps_r)
+    F, B = oracle.ml(I, np.ones(I.shape[:2]), p)
+    dev = np.abs(F - I).max()
+    assert np.all(B == 0.0)
+    assert 0 < dev <= bound + 1e-12
+    F, B = oracle.ml(I, np.zeros(I.shape[:2]), p)
+    assert np.all(F == 0.0)
+    assert 0 < np.abs(B - I).max() <= bound + 1e-12
+
+
 def test_alpha_complement_swaps_foreground_and_background():
     I, a = _inputs(23, 31, 6, grid=True)
     F, B = oracle.ml(I, a)
